@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the w-projection gridding path on GB300 (one JSON line on stdout).
+
+A step is one imaging pass over one batch with all inputs resident in HBM: grid_zero,
+vis_compress (placement, compression, compaction, normaliser), grid_vis (the gridder) and
+grid_correct (inverse FFT, normalisation, taper and sinc correction, Stokes I).  The table
+build is one-off and outside the timed region, as in the thesis (Sec. 5.3.1 times the
+gridder only).  Inputs (6.2 GB for the default workload) are larger than L2.
+
+value  = total grid-point updates per second of the whole step, summed over ranks: every
+         griddable record x S^2 x polarisations, compressed records included as if gridded
+         (the thesis's "total rate", Sec. 5.3.1); the "real" rate counts only the updates the
+         gridder performed.
+e2e    = the same metric with pinned host inputs copied to the device and the Stokes-I image
+         copied back inside the timed region of every step.
+roofline = the gridder kernel against the FP32 FMA pipe (8 flops per update, Sec. 5.4.4).
+
+`--impl reference` times the FP64 CPU oracle on the host cores on bounded samples of the
+same workload (only rank 0 runs it under torchrun).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "wproj_2k": "64 stations (3 km Gaussian), 2016 baselines x 3600 steps at 1 s, 16 channels 120-180 MHz, "
+                "4 pols, complex64; grid 2048^2 x 16 ch; 32 sqrt(w)-spaced w-planes, supports 9..65; "
+                "beta=8; FP32 table; compression on",
+    "w0_small": "32 stations (2 km disk), 496 baselines x 256 steps at 10 s, 1 channel 150 MHz, 1 pol; "
+                "grid 512^2; w=0, support 7, beta=8; compression off",
+}
+# bounded CPU samples of the same geometry (channels, time steps)
+CPU_SAMPLE = {"wproj_2k": (4, 1200), "w0_small": (1, 256)}
+REF_SAMPLE = {"wproj_2k": (2, 360), "w0_small": (1, 256)}
+COMPRESS = {"wproj_2k": True, "w0_small": False}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _gridder_traffic(per_launch_units):
+    """DRAM bytes per k_grid launch from the committed ncu summary, scaled to this launch's
+    gridded updates; None if the gridder source changed since the counters were taken."""
+    prof = os.path.join(ROOT, "profiles", "k_grid_wproj_2k.md")
+    src = os.path.join(ROOT, "paper_1403_4209_gb300", "csrc", "grid.cu")
+    if not os.path.exists(prof):
+        return None
+    kv = {}
+    with open(prof) as f:
+        for line in f:
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                kv[k.strip()] = v.strip().strip("`")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if kv.get("grid.cu sha256[:16]") != h:
+            return None
+        return float(kv["dram bytes per update"]) * per_launch_units
+    except (KeyError, ValueError):
+        return None
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_1403_4209_gb300 as wg
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = "cuda:%d" % local_rank
+    wl = synth.make(args.workload, device=dev, n_chan=args.n_chan, n_times=args.n_times)
+    tab = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+    g = wg.Grid(wl.n_grid, wl.du, wl.n_pol, wl.n_chan, device=dev)
+    uvw_d = torch.as_tensor(wl.uvw, device=dev)
+    freq_d = torch.as_tensor(wl.freq, device=dev)
+    batch = wg.VisBatch(uvw_d, freq_d, wl.vis, wl.weight, wl.flag)
+    wlst = wg.WorkList(wl.rows * wl.n_chan, wl.n_chan, wl.n_pol)
+    img = torch.empty((wl.n_chan, wl.n_grid, wl.n_grid), dtype=torch.float32, device=dev)
+    compress = COMPRESS[args.workload]
+    stream = torch.cuda.current_stream()
+    ev_g = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def step(k=None):
+        g.zero()
+        wg.vis_compress(g, tab, batch, wlst, compress=compress)
+        if k is not None:
+            ev_g[k][0].record(stream)
+        wg.grid_vis(g, tab, wlst)
+        if k is not None:
+            ev_g[k][1].record(stream)
+        wg.grid_correct(g, tab, mode=wg.IMAGE_STOKES_I, out=img)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = wlst.stats()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    n0 = wg.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = wg.launch_count() - n0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t_grid = sum(a.elapsed_time(b) for a, b in ev_g) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    real = st["updates"]
+    total = st["updates"] + st["updates_saved"]
+    value = world * total / (ms * 1e-3) / 1e9
+
+    # degridding of the same batch (predict mode), timed separately
+    out_v = torch.empty_like(wl.vis)
+    for _ in range(2):
+        wg.degrid_vis(g, tab, batch, wlst, out=out_v)
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    nd = max(3, args.steps // 2)
+    for _ in range(nd):
+        wg.degrid_vis(g, tab, batch, wlst, out=out_v)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    t_degrid = d0.elapsed_time(d1) / nd
+
+    # end to end: pinned host inputs -> device, step, Stokes-I image -> pinned host
+    h_uvw = torch.as_tensor(wl.uvw).pin_memory()
+    h_vis = wl.vis.cpu().pin_memory()
+    h_w = wl.weight.cpu().pin_memory()
+    h_f = wl.flag.cpu().pin_memory()
+    h_img = torch.empty(img.shape, dtype=img.dtype).pin_memory()
+    h2d = h_uvw.numel() * 8 + h_vis.numel() * 8 + h_w.numel() * 4 + h_f.numel() + freq_d.numel() * 8
+    d2h = h_img.numel() * 4
+
+    def e2e_step():
+        uvw_d.copy_(h_uvw, non_blocking=True)
+        batch.vis.copy_(h_vis, non_blocking=True)
+        batch.weight.copy_(h_w, non_blocking=True)
+        batch.flag.copy_(h_f, non_blocking=True)
+        step()
+        h_img.copy_(img, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ne = max(3, args.steps // 2)
+    x0.record(stream)
+    for _ in range(ne):
+        e2e_step()
+    x1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = x0.elapsed_time(x1) / ne
+    if world > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+
+    peaks, src = _peaks()
+    props = torch.cuda.get_device_properties(local_rank)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = 8.0 * real / (t_grid * 1e-3) / 1e12
+    traffic = _gridder_traffic(real)
+
+    line = {
+        "metric": "gridding/degridding G grid-point updates/s and % roofline at stated grid error",
+        "value": round(value, 3),
+        "unit": "G grid-point updates/s (total rate, whole step)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "%s: %s%s" % (args.workload, WORKLOADS[args.workload],
+                                              "" if args.n_chan is None and args.n_times is None else
+                                              " (slice: %s channels, %s steps)" % (args.n_chan, args.n_times)),
+                   "records_per_step": wl.rows * wl.n_chan, "l2": "inputs larger than L2 (no flush needed)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "rates": {"total_step_G": round(value, 3),
+                  "real_step_G": round(world * real / (ms * 1e-3) / 1e9, 3),
+                  "real_gridder_G": round(real / (t_grid * 1e-3) / 1e9, 3),
+                  "total_gridder_G": round(total / (t_grid * 1e-3) / 1e9, 3),
+                  "degrid_G": round(total / (t_degrid * 1e-3) / 1e9, 3),
+                  "gridder_ms": round(t_grid, 4), "degrid_ms": round(t_degrid, 4),
+                  "records_gridded": st["gridded"], "records_compressed": st["compressed"],
+                  "updates_real": real, "updates_total": total},
+        "roofline": {"kernel": "k_grid", "bound": "alu", "achieved": round(achieved, 3),
+                     "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
+                     "frac": round(achieved / peak_tflops, 4),
+                     "peak_source": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flops x %.0f MHz (%s sm_max_mhz)"
+                                    % (props.multi_processor_count, sm_mhz, src),
+                     "traffic": traffic},
+        "e2e": {"value": round(world * total / (ms_e2e * 1e-3) / 1e9, 3), "unit": "G grid-point updates/s",
+                "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_sample(args.workload, *CPU_SAMPLE[args.workload])
+    return line
+
+
+def cpu_sample(workload, n_chan, n_times):
+    """The FP64 oracle (placement, compression, gridding) on a bounded sample, same geometry."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    wl = synth.make(workload, n_chan=n_chan, n_times=n_times)
+    ot = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+    vis, w, f = wl.vis.numpy(), wl.weight.numpy(), wl.flag.numpy()
+    t0 = time.perf_counter()
+    pl = oracle.place(wl.uvw, wl.freq, wl.du, wl.n_grid, ot, flag=f)
+    if COMPRESS[workload]:
+        g, c = oracle.classify(pl)
+        oracle.grid_compressed(pl, ot, vis, w, f, wl.n_grid)
+    else:
+        g, c = pl.griddable, np.zeros_like(pl.griddable)
+        oracle.grid_plain(pl, ot, vis, w, f, wl.n_grid)
+    dt = time.perf_counter() - t0
+    st = oracle.stats(pl, g, c)
+    total = (st["updates"] + st["updates_saved"]) * wl.n_pol
+    return {"value": round(total / dt / 1e9, 4), "unit": "G grid-point updates/s (total rate)", "cores": 1,
+            "kind": "oracle", "seconds": round(dt, 2),
+            "sample": "%s geometry, %d channels x %d time steps x %d baselines (%d records), FP64 oracle: "
+                      "placement + compression + gridding, single thread" % (
+                          workload, n_chan, n_times, wl.n_baselines, wl.rows * wl.n_chan)}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step one bounded sample on the host cores."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    n_chan, n_times = REF_SAMPLE[args.workload]
+    wl = synth.make(args.workload, n_chan=n_chan, n_times=n_times)
+    ot = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+    vis, w, f = wl.vis.numpy(), wl.weight.numpy(), wl.flag.numpy()
+
+    def step():
+        pl = oracle.place(wl.uvw, wl.freq, wl.du, wl.n_grid, ot, flag=f)
+        if COMPRESS[args.workload]:
+            g, c = oracle.classify(pl)
+            oracle.grid_compressed(pl, ot, vis, w, f, wl.n_grid)
+        else:
+            g, c = pl.griddable, np.zeros_like(pl.griddable)
+            oracle.grid_plain(pl, ot, vis, w, f, wl.n_grid)
+        return oracle.stats(pl, g, c)
+
+    for _ in range(args.warmup):
+        st = step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = step()
+    dt = (time.perf_counter() - t0) / args.steps
+    total = (st["updates"] + st["updates_saved"]) * wl.n_pol
+    value = total / dt / 1e9
+    unit = "G grid-point updates/s (total rate, whole step)"
+    sample = ("%s geometry, %d channels x %d time steps x %d baselines (%d records) per step" %
+              (args.workload, n_chan, n_times, wl.n_baselines, wl.rows * wl.n_chan))
+    return {
+        "impl": "reference",
+        "metric": "gridding/degridding G grid-point updates/s and % roofline at stated grid error",
+        "value": round(value, 4), "unit": unit, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "%s: %s%s" % (args.workload, WORKLOADS[args.workload],
+                                              "" if args.n_chan is None and args.n_times is None else
+                                              " (slice: %s channels, %s steps)" % (args.n_chan, args.n_times)), "sample": sample},
+        "cpu_baseline": {"value": round(value, 4), "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wproj_2k")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-chan", type=int, default=None, help="run a slice: first n channels (profiling)")
+    ap.add_argument("--n-times", type=int, default=None, help="run a slice: n time steps (profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * wgrid.h -- C ABI of the GB300 w-projection gridder/degridder with compression.
+ *
+ * Operation: convolutional gridding with w-projection (thesis Sec. 2.1-2.2, eqs.
+ * "convgrid", "C_W") as restated for the WImager algorithm (Sec. 4.3.2, eq. "gridding"),
+ * with the thesis's compression of consecutive records (Sec. 4.3.3, eq. "compression"),
+ * the convolution-function generator (Sec. 4.2, Algorithm "convgen") and the image
+ * finaliser (Sec. 4.7, Algorithm "finalizer").  Degridding, the exact adjoint of
+ * gridding, is not in the thesis.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: WG_OK (0) or a negative WG_E_* code.  No C++
+ *     exception crosses this boundary.  wg_last_error() returns a thread-local message
+ *     describing the most recent failure on the calling thread.
+ *   - Pointers documented "device" must point to CUDA device memory of the current device;
+ *     they are owned by the caller and must stay valid until the stream work that uses
+ *     them has completed.  Opaque handles (wg_grid, wg_table, wg_worklist) are owned by the
+ *     library and released by the matching *_destroy function.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Every
+ *     call that takes a stream only enqueues work on it and returns without synchronising,
+ *     except where a comment says "synchronises".
+ *   - Record layout: a record is one (row, channel) pair with n_pol polarisations.  Rows are
+ *     expected grouped by baseline and sorted by time (Sec. 4.3: compression and the
+ *     gridder's register accumulation rely on it; any order is still correct).
+ *   - Grid layout: complex64 (float re, float im) [n_chan][N][N][n_pol]; pixel (y, x) holds
+ *     n_pol polarisations; (0,0) is the most negative (u, v); u = v = 0 at index N/2
+ *     (Sec. 4.3.3).  One grid per channel (Sec. 4.1: channels are imaged independently).
+ *   - Coordinates decide placement in FP64 exactly as stated at vis_compress(); the
+ *     accumulation is FP32.
+ */
+#ifndef WGRID_H
+#define WGRID_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+#define WG_OK 0
+#define WG_E_INVALID_ARG (-1) /* null pointer, bad enum, inconsistent sizes            */
+#define WG_E_SHAPE (-2)       /* grid / table / input dimensions do not match          */
+#define WG_E_OOB_SUPPORT (-3) /* support larger than the grid or the implementation    */
+#define WG_E_CUDA (-4)        /* a CUDA runtime or cuFFT call failed                   */
+#define WG_E_OOM (-5)         /* device allocation failed                              */
+#define WG_E_CAPACITY (-6)    /* input larger than the worklist was created for        */
+
+/* element types */
+#define WG_F32 0  /* kernel table stored as complex float32                        */
+#define WG_BF16 1 /* kernel table stored as complex bfloat16 (reserved)            */
+#define WG_F16 2  /* kernel table stored as complex float16 (reserved)             */
+
+/* support modes of conv_table_build */
+#define WG_SUPPORT_THRESHOLD 0  /* outermost sample with |C| > threshold (Sec. 4.2.3) */
+#define WG_SUPPORT_PRESCRIBED 1 /* trim or zero-pad to given supports ("normal" mode,
+                                   Sec. 4.2.1), one odd support per w-plane          */
+
+/* degrid_vis modes */
+#define WG_DEGRID_PREDICT 0 /* model visibilities: psi-conjugated kernel sums          */
+#define WG_DEGRID_ADJOINT 1 /* exact adjoint of the vis -> grid map (also eps (1-f))   */
+
+/* grid_correct modes */
+#define WG_IMAGE_PER_POL 0 /* output float [n_chan][n_pol][N][N]                      */
+#define WG_IMAGE_STOKES_I 1 /* output float [n_chan][N][N]: mean of pols 0 and P-1     */
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* wg_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far (all devices).
+ * Library FFT kernels (cuFFT) are not counted. */
+uint64_t wg_launch_count(void);
+
+/* ---- grid (output O-1 and O-2 of Sec. 4.3.2) --------------------------------------- */
+typedef struct wg_grid wg_grid;
+
+typedef struct wg_grid_desc {
+    int32_t n;      /* grid side N, even, 8 <= N <= 32768                                */
+    int32_t n_pol;  /* polarisations per pixel: 1, 2 or 4                                */
+    int32_t n_chan; /* channels (independent grids), >= 1                                */
+    int32_t reserved;
+    double du;      /* cell size Delta u = Delta v in wavelengths, > 0                    */
+    void* data;     /* optional caller-owned device buffer of n_chan*N*N*n_pol complex64 */
+                    /* (8-byte aligned); NULL: the library allocates and owns it          */
+} wg_grid_desc;
+
+/* Creates a grid and its FP64 normaliser accumulators N_p [n_chan][n_pol] (eq.
+ * "normalizer"), both zeroed.  Synchronises the device.  Errors: INVALID_ARG, OOM, CUDA. */
+int grid_create(const wg_grid_desc* desc, wg_grid** out);
+int grid_destroy(wg_grid* grid);
+/* Zeroes the grid, the normaliser and the statistics counters on `stream`. */
+int grid_zero(wg_grid* grid, void* stream);
+/* Device pointers of the grid data (complex64, layout above) and of N_p (double
+ * [n_chan][n_pol]).  Either output may be NULL. */
+int grid_device_ptrs(const wg_grid* grid, void** data, double** normaliser);
+
+/* ---- convolution functions (inputs C-1, C-2, C-3 of Sec. 4.2.2) -------------------- */
+typedef struct wg_table wg_table;
+
+typedef struct wg_table_desc {
+    int32_t n_wplanes;     /* K >= 1; plane k has w_k = w_max (k/(K-1))^2 (sqrt-w spacing) */
+    int32_t oversample;    /* beta, 1 <= beta <= 64                                       */
+    int32_t taper_support; /* S0: the prolate spheroidal taper has bandwidth c = pi S0 / 2 */
+    int32_t n_k;           /* image-plane patch side N_k (even, >= 8); 0 = max(64, next    */
+                           /* power of two >= 2 * largest support) or 256 (threshold mode) */
+    int32_t support_mode;  /* WG_SUPPORT_THRESHOLD or WG_SUPPORT_PRESCRIBED               */
+    int32_t store_dtype;   /* WG_F32                                                      */
+    double w_max;          /* largest |w| in wavelengths (> 0 if K > 1)                    */
+    double du;             /* cell size in wavelengths; must equal the grid's              */
+    double threshold;      /* support threshold on |C| (thesis: 1e-3)                      */
+    const int32_t* supports; /* host [K] odd supports for WG_SUPPORT_PRESCRIBED, else NULL */
+} wg_table_desc;
+
+/* Algorithm "convgen" on the GPU: per plane, sample taper(l) taper(m) exp(+j2pi w (n-1))
+ * on an N_k x N_k patch covering the field of view, zero-pad to beta N_k, FFT (cuFFT,
+ * FP64), normalise by C_0(0,0), find or apply the support, trim into beta^2 sub-kernels
+ * of S x S row-major samples ordered (dv, du) (C-1), plane supports and offsets (C-2),
+ * and zeta = sum of the real parts of each sub-kernel (C-3, FP64).
+ * Synchronises `stream` (supports are read back, as in the thesis).
+ * Errors: INVALID_ARG (even or non-positive support, beta or K out of range),
+ *         OOB_SUPPORT (support > 1023), OOM, CUDA. */
+int conv_table_build(const wg_table_desc* desc, wg_table** out, void* stream);
+
+/* Builds a table from caller-provided host data in the same layout as C-1/C-2/C-3:
+ * data = complex double [sum_k beta^2 S_k^2] (interleaved re, im), supports [K] (odd),
+ * zeta [K beta^2].  Stored as complex float32.  Synchronises the device. */
+int conv_table_import(int32_t n_wplanes, int32_t oversample, double w_max, double du,
+                      int32_t taper_support, const int32_t* supports, const double* data,
+                      const double* zeta, wg_table** out);
+int table_destroy(wg_table* table);
+
+typedef struct wg_table_info {
+    int32_t n_wplanes, oversample, taper_support, max_support;
+    int64_t n_samples;        /* total complex samples in C-1                         */
+    double w_max, du;
+    const void* data;         /* device complex float32 [n_samples]                   */
+    const double* zeta;       /* device double [K beta^2]                              */
+    const int32_t* supports;  /* device int32 [K]                                      */
+    const int32_t* offsets;   /* device int32 [K] first sample of each plane           */
+} wg_table_info;
+int table_info(const wg_table* table, wg_table_info* info);
+/* Copies C-1 (complex float32, interleaved), C-3 and C-2 to host buffers sized from
+ * table_info; any pointer may be NULL.  Synchronises the device. */
+int table_copy_to_host(const wg_table* table, float* data, double* zeta, int32_t* supports,
+                       int32_t* offsets);
+
+/* ---- visibility input (inputs I-1 .. I-5 of Sec. 4.3.2) ----------------------------- */
+typedef struct wg_vis_in {
+    int64_t n_rows;         /* rows (baseline-major, time-minor)                          */
+    int32_t n_chan;         /* must equal the grid's                                       */
+    int32_t n_pol;          /* must equal the grid's                                       */
+    const double* uvw;      /* device [n_rows][3] baseline in metres (I-1)                */
+    const double* freq_hz;  /* device [n_chan] channel frequencies (I-2: lambda^-1 = f/c) */
+    const void* vis;        /* device [n_rows][n_chan][n_pol] complex64 (I-5)             */
+    const float* weight;    /* device [n_rows][n_chan][n_pol] natural weights (I-3)       */
+    const uint8_t* flag;    /* device [n_rows][n_chan][n_pol], 1 = flagged (I-4)          */
+} wg_vis_in;
+
+/* ---- work list: the preparation phase's outputs (Sec. 4.3.4) ----------------------- */
+typedef struct wg_worklist wg_worklist;
+
+/* Allocates device buffers for up to max_records = n_rows * n_chan records.
+ * Errors: INVALID_ARG, OOM. */
+int worklist_create(int64_t max_records, int32_t n_chan, int32_t n_pol, wg_worklist** out);
+int worklist_destroy(wg_worklist* wl);
+
+typedef struct wg_stats {
+    int64_t records;         /* records presented                                         */
+    int64_t griddable;       /* records with g + c = 1                                    */
+    int64_t gridded;         /* sum g (Sec. 4.3.4)                                        */
+    int64_t compressed;      /* sum c                                                     */
+    int64_t updates;         /* sum g S^2 * n_pol: grid-point updates done by the gridder */
+    int64_t updates_saved;   /* sum c S^2 * n_pol: updates saved by compression           */
+    int64_t tasks;           /* gridder work items                                        */
+    int64_t dropped;         /* entries rejected by device-side bounds checks (always 0;  */
+                             /* nonzero means an internal error, the entries were skipped)*/
+} wg_stats;
+
+/* Preparation phase (Sec. 4.3.4) for one batch, on `stream`:
+ *   A1 placement, per record (row r, channel c), FP64, each operation rounded once:
+ *      lam_inv = f_c / 299792458;  sc = lam_inv * (beta / du)
+ *      tu = u' sc, tv = v' sc, w = w' lam_inv;  if w' < 0: negate all three, psi = -1
+ *      q = ceil(t - 0.5);  x_c = ceil((q - beta/2) / beta) (integer);  frac = q - beta x_c
+ *      x = N/2 + x_c;  k = floor((K-1) sqrt(w / w_max) + 0.5)  (k = 0 if K = 1)
+ *      footprint origin (x - (S_k-1)/2, y - (S_k-1)/2); kernel pointer
+ *      z = offset_k + ((frac_v - lo) beta + (frac_u - lo)) S_k^2, lo = -((beta-1)/2)
+ *      griddable: k <= K-1, footprint inside the grid, some polarisation unflagged;
+ *   A2 compression (if `compress` != 0): record (r, c) is compressed into (r-1, c) when
+ *      both are griddable with equal footprint origin and z (eq. "ci");
+ *   A3 compaction of gridded records into channel-major lists, segmented into tasks;
+ *   A4 gamma = sum over each run of eps (1-f) psi-conj(vis) (eqs. "compress1",
+ *      "conjugatetake"), FP32;
+ *   A5 the normaliser terms and statistics, added into the grid's N_p and counters when
+ *      grid_vis runs.
+ * `grid` supplies N and du; `table` the planes, supports and zeta.  The work list keeps
+ * the results until the next call on it.
+ * Errors: INVALID_ARG, SHAPE (n_chan/n_pol/du mismatch), CAPACITY, CUDA. */
+int vis_compress(const wg_grid* grid, const wg_table* table, const wg_vis_in* in,
+                 int32_t compress, wg_worklist* wl, void* stream);
+
+/* Copies the work list's statistics (Sec. 4.3.4) to *out.  Synchronises `stream`. */
+int worklist_stats(const wg_worklist* wl, wg_stats* out, void* stream);
+
+/* Device views of the work list, for inspection and tests.  entries: int32 [n][4] with
+ * {x0 | y0 << 16, (-x0 mod S) | (-y0 mod S) << 16, z, k | chan << 16}; gamma: complex64
+ * [n][n_pol]; runs: int32 [n][2] first and last row of each gridded run; rec_class: uint8
+ * per input record, bit0 = g, bit1 = c, bit2 = griddable.  *n_entries is read from the
+ * device (synchronises `stream`). */
+int worklist_view(const wg_worklist* wl, const int32_t** entries, const void** gamma,
+                  const int32_t** runs, const uint8_t** rec_class, int64_t* n_entries,
+                  void* stream);
+
+/* A6: adds every gridded record's gamma_p * C_k[i][j] to grid pixel (y0+i, x0+j) (eq.
+ * "gridding"), FP32 accumulation, and adds the batch's normaliser terms and statistics
+ * into the grid.  Persistent kernel over the work list's tasks.  Errors: SHAPE, CUDA. */
+int grid_vis(wg_grid* grid, const wg_table* table, const wg_worklist* wl, void* stream);
+
+/* A7 (not in the thesis): for every input record, m_p = sum_ij conj(C_k[i][j]) grid_p(y0+i,
+ * x0+j), conjugated back where psi = -1; WG_DEGRID_ADJOINT also multiplies by eps (1-f).
+ * Records that are not griddable get 0.  `in` and `wl` must be the batch given to the
+ * last vis_compress on `wl`.  vis_out: device complex64 [n_rows][n_chan][n_pol],
+ * overwritten.  Errors: INVALID_ARG, SHAPE, CUDA. */
+int degrid_vis(const wg_grid* grid, const wg_table* table, const wg_vis_in* in,
+               const wg_worklist* wl, int32_t mode, void* vis_out, void* stream);
+
+/* A9, Algorithm "finalizer": inverse FFT per polarisation (cuFFT, FP32, centred so that
+ * image pixel N/2 is l = 0), real part, divide by N_p, by the taper psi_0(c, 2 du l)
+ * psi_0(c, 2 du m) and by sinc(pi l du / beta) sinc(pi m du / beta), l = (k - N/2)/(N du).
+ * image_out: device float, layout per `mode`.  The grid is not modified.
+ * Errors: INVALID_ARG, SHAPE, CUDA. */
+int grid_correct(wg_grid* grid, const wg_table* table, int32_t mode, float* image_out,
+                 void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WGRID_H */

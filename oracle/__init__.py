@@ -27,7 +27,7 @@ closed forms, brute force, invariants and worked counts from the thesis.  Parity
 unpinned: absolute kernel values for the exact (non-paraxial) w-screen at large w
 beyond brute-force sizes -- the thesis prints no kernel values.
 """
-from .lib import lib  # noqa: F401  (compiles oracle.c on first use)
+from .cloops import lib  # noqa: F401  (compiles oracle.c on first use)
 from .pswf import psi0
 from .table import Table, build_table, delta_table
 from .place import place, classify, Placement

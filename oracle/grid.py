@@ -12,7 +12,7 @@ degrid           : adjoint of the gridding map.  The vis -> grid map is only R-l
 """
 import numpy as np
 
-from .lib import lib
+from .cloops import lib
 
 
 def _p(a):

@@ -1,0 +1,390 @@
+// C-ABI entry points of include/wgrid.h: argument validation, handle lifetime, error reporting.
+#include <cstdarg>
+#include <cstdio>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+struct wg_grid { wg::Grid g; };
+struct wg_table { wg::Table t; };
+struct wg_worklist { wg::WorkList w; };
+
+namespace wg {
+
+std::atomic<uint64_t> g_launches{0};
+static thread_local char t_err[512] = "";
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_err, sizeof(t_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? WG_E_OOM : WG_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int num_sms()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+}  // namespace wg
+
+using namespace wg;
+
+static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+const char* wg_last_error(void) { return t_err; }
+
+uint64_t wg_launch_count(void) { return g_launches.load(); }
+
+// ---- grid -----------------------------------------------------------------------------
+int grid_create(const wg_grid_desc* d, wg_grid** out)
+{
+    t_err[0] = 0;
+    if (!d || !out) return fail(WG_E_INVALID_ARG, "grid_create: null argument");
+    *out = nullptr;
+    if (d->n < 8 || d->n > 32768 || (d->n & 1)) return fail(WG_E_INVALID_ARG, "grid side N=%d must be even in [8, 32768]", d->n);
+    if (d->n_pol != 1 && d->n_pol != 2 && d->n_pol != 4) return fail(WG_E_INVALID_ARG, "n_pol=%d must be 1, 2 or 4", d->n_pol);
+    if (d->n_chan < 1 || d->n_chan > 4096) return fail(WG_E_INVALID_ARG, "n_chan=%d must be in [1, 4096]", d->n_chan);
+    if (!(d->du > 0.0)) return fail(WG_E_INVALID_ARG, "cell size du must be positive");
+    if (d->data && (reinterpret_cast<uintptr_t>(d->data) & 15)) return fail(WG_E_INVALID_ARG, "external grid buffer must be 16-byte aligned");
+    wg_grid* h = new (std::nothrow) wg_grid;
+    if (!h) return fail(WG_E_OOM, "host allocation failed");
+    Grid& g = h->g;
+    g.n = d->n;
+    g.n_pol = d->n_pol;
+    g.n_chan = d->n_chan;
+    g.du = d->du;
+    const size_t bytes = sizeof(float2) * (size_t)g.n * g.n * g.n_pol * g.n_chan;
+    if (d->data) {
+        g.data = static_cast<float2*>(d->data);
+    } else {
+        if (cudaMalloc(&g.data, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return fail(WG_E_OOM, "cannot allocate a %zu-byte grid", bytes);
+        }
+        g.owns = true;
+    }
+    if (cudaMalloc(&g.norm, sizeof(double) * g.n_chan * g.n_pol) != cudaSuccess ||
+        cudaMalloc(&g.counters, sizeof(unsigned long long) * ST_N) != cudaSuccess) {
+        cudaGetLastError();
+        grid_destroy(h);
+        return fail(WG_E_OOM, "cannot allocate normaliser");
+    }
+    int rc = grid_zero(h, nullptr);
+    if (rc == WG_OK && cudaDeviceSynchronize() != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "grid_create");
+    if (rc != WG_OK) {
+        grid_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return WG_OK;
+}
+
+int grid_destroy(wg_grid* h)
+{
+    if (!h) return WG_OK;
+    Grid& g = h->g;
+    if (g.owns) cudaFree(g.data);
+    cudaFree(g.norm);
+    cudaFree(g.counters);
+    cudaFree(g.scratch);
+    cudaFree(g.corr);
+    if (g.plan_ok) cufftDestroy(g.plan);
+    delete h;
+    return WG_OK;
+}
+
+int grid_zero(wg_grid* h, void* stream)
+{
+    if (!h) return fail(WG_E_INVALID_ARG, "grid_zero: null grid");
+    Grid& g = h->g;
+    WG_CUDA(cudaMemsetAsync(g.data, 0, sizeof(float2) * (size_t)g.n * g.n * g.n_pol * g.n_chan, S(stream)));
+    WG_CUDA(cudaMemsetAsync(g.norm, 0, sizeof(double) * g.n_chan * g.n_pol, S(stream)));
+    WG_CUDA(cudaMemsetAsync(g.counters, 0, sizeof(unsigned long long) * ST_N, S(stream)));
+    return WG_OK;
+}
+
+int grid_device_ptrs(const wg_grid* h, void** data, double** normaliser)
+{
+    if (!h) return fail(WG_E_INVALID_ARG, "grid_device_ptrs: null grid");
+    if (data) *data = h->g.data;
+    if (normaliser) *normaliser = h->g.norm;
+    return WG_OK;
+}
+
+// ---- table ----------------------------------------------------------------------------
+int conv_table_build(const wg_table_desc* d, wg_table** out, void* stream)
+{
+    t_err[0] = 0;
+    if (!d || !out) return fail(WG_E_INVALID_ARG, "conv_table_build: null argument");
+    *out = nullptr;
+    if (d->n_wplanes < 1 || d->n_wplanes > 4095) return fail(WG_E_INVALID_ARG, "n_wplanes=%d must be in [1, 4095]", d->n_wplanes);
+    if (d->oversample < 1 || d->oversample > kMaxBeta) return fail(WG_E_INVALID_ARG, "oversample=%d must be in [1, %d]", d->oversample, kMaxBeta);
+    if (d->taper_support < 1 || d->taper_support > 255) return fail(WG_E_INVALID_ARG, "taper_support=%d must be in [1, 255]", d->taper_support);
+    if (d->n_k != 0 && (d->n_k < 8 || (d->n_k & 1))) return fail(WG_E_INVALID_ARG, "n_k=%d must be 0 or even >= 8", d->n_k);
+    if (!(d->du > 0.0)) return fail(WG_E_INVALID_ARG, "du must be positive");
+    if (d->n_wplanes > 1 && !(d->w_max > 0.0)) return fail(WG_E_INVALID_ARG, "w_max must be positive with more than one w-plane");
+    if (d->store_dtype != WG_F32) return fail(WG_E_INVALID_ARG, "store_dtype %d not supported", d->store_dtype);
+    if (d->support_mode == WG_SUPPORT_PRESCRIBED) {
+        if (!d->supports) return fail(WG_E_INVALID_ARG, "prescribed supports missing");
+        for (int k = 0; k < d->n_wplanes; ++k) {
+            if (d->supports[k] < 1 || d->supports[k] % 2 == 0) return fail(WG_E_INVALID_ARG, "support %d of plane %d must be odd and positive", d->supports[k], k);
+            if (d->supports[k] > kMaxSupport) return fail(WG_E_OOB_SUPPORT, "support %d of plane %d exceeds %d", d->supports[k], k, kMaxSupport);
+        }
+    } else if (d->support_mode == WG_SUPPORT_THRESHOLD) {
+        if (!(d->threshold > 0.0)) return fail(WG_E_INVALID_ARG, "threshold must be positive");
+    } else {
+        return fail(WG_E_INVALID_ARG, "unknown support_mode %d", d->support_mode);
+    }
+    wg_table* h = new (std::nothrow) wg_table;
+    if (!h) return fail(WG_E_OOM, "host allocation failed");
+    int rc = build_table(*d, h->t, S(stream));
+    if (rc != WG_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return WG_OK;
+}
+
+int conv_table_import(int32_t K, int32_t beta, double w_max, double du, int32_t s0, const int32_t* supports,
+                      const double* data, const double* zeta, wg_table** out)
+{
+    t_err[0] = 0;
+    if (!supports || !data || !zeta || !out) return fail(WG_E_INVALID_ARG, "conv_table_import: null argument");
+    *out = nullptr;
+    if (K < 1 || K > 4095 || beta < 1 || beta > kMaxBeta || !(du > 0.0) || s0 < 1 || s0 > 255)
+        return fail(WG_E_INVALID_ARG, "conv_table_import: K, beta, du or taper support out of range");
+    if (K > 1 && !(w_max > 0.0)) return fail(WG_E_INVALID_ARG, "w_max must be positive with more than one w-plane");
+    wg_table* h = new (std::nothrow) wg_table;
+    if (!h) return fail(WG_E_OOM, "host allocation failed");
+    int rc = import_table(K, beta, w_max, du, s0, supports, data, zeta, h->t);
+    if (rc != WG_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return WG_OK;
+}
+
+int table_destroy(wg_table* h)
+{
+    if (!h) return WG_OK;
+    free_table(h->t);
+    delete h;
+    return WG_OK;
+}
+
+int table_info(const wg_table* h, wg_table_info* info)
+{
+    if (!h || !info) return fail(WG_E_INVALID_ARG, "table_info: null argument");
+    const Table& t = h->t;
+    info->n_wplanes = t.K;
+    info->oversample = t.beta;
+    info->taper_support = t.s0;
+    info->max_support = t.max_support;
+    info->n_samples = t.n_samples;
+    info->w_max = t.w_max;
+    info->du = t.du;
+    info->data = t.data;
+    info->zeta = t.zeta;
+    info->supports = t.supports_d;
+    info->offsets = t.offsets_d;
+    return WG_OK;
+}
+
+int table_copy_to_host(const wg_table* h, float* data, double* zeta, int32_t* supports, int32_t* offsets)
+{
+    if (!h) return fail(WG_E_INVALID_ARG, "table_copy_to_host: null table");
+    const Table& t = h->t;
+    if (data) WG_CUDA(cudaMemcpy(data, t.data, sizeof(float2) * t.n_samples, cudaMemcpyDeviceToHost));
+    if (zeta) WG_CUDA(cudaMemcpy(zeta, t.zeta, sizeof(double) * t.K * t.beta * t.beta, cudaMemcpyDeviceToHost));
+    if (supports) std::memcpy(supports, t.supports.data(), sizeof(int) * t.K);
+    if (offsets) std::memcpy(offsets, t.offsets.data(), sizeof(int) * t.K);
+    return WG_OK;
+}
+
+// ---- work list ------------------------------------------------------------------------
+int worklist_destroy(wg_worklist* h)
+{
+    if (!h) return WG_OK;
+    WorkList& w = h->w;
+    void* ptrs[] = {w.rinfo, w.rclass, w.tile_cnt, w.entries, w.gamma, w.runs, w.seg_nblk, w.seg_off,
+                    w.scal, w.chan_base, w.norm_priv, w.norm_batch, w.stat_priv, w.stats, w.task_counter};
+    for (void* p : ptrs) cudaFree(p);
+    delete h;
+    return WG_OK;
+}
+
+int worklist_create(int64_t max_records, int32_t C, int32_t P, wg_worklist** out)
+{
+    t_err[0] = 0;
+    if (!out) return fail(WG_E_INVALID_ARG, "worklist_create: null argument");
+    *out = nullptr;
+    if (max_records < 1 || max_records > ((int64_t)1 << 31) - 1)
+        return fail(WG_E_INVALID_ARG, "max_records=%lld must be in [1, 2^31 - 1]", (long long)max_records);
+    if (C < 1 || C > 4096) return fail(WG_E_INVALID_ARG, "n_chan=%d must be in [1, 4096]", C);
+    if (P != 1 && P != 2 && P != 4) return fail(WG_E_INVALID_ARG, "n_pol=%d must be 1, 2 or 4", P);
+    wg_worklist* h = new (std::nothrow) wg_worklist;
+    if (!h) return fail(WG_E_OOM, "host allocation failed");
+    WorkList& w = h->w;
+    w.cap = max_records;
+    w.C = C;
+    w.P = P;
+    const int rpb = std::max(1, kTileRecords / C);
+    const int64_t rows_max = (max_records + C - 1) / C;
+    w.tile_cap = ((rows_max + rpb - 1) / rpb + 2) * C;
+    w.seg_cap = max_records / kSegLen + 2;
+    bool ok = true;
+    auto al = [&](void** p, size_t bytes) {
+        if (ok && cudaMalloc(p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+        }
+    };
+    al((void**)&w.rinfo, sizeof(int4) * max_records);
+    al((void**)&w.rclass, max_records);
+    al((void**)&w.tile_cnt, sizeof(int) * w.tile_cap);
+    al((void**)&w.entries, sizeof(int4) * max_records);
+    al((void**)&w.gamma, sizeof(float2) * max_records * P);
+    al((void**)&w.runs, sizeof(int2) * max_records);
+    al((void**)&w.seg_nblk, sizeof(int) * w.seg_cap);
+    al((void**)&w.seg_off, sizeof(int) * (w.seg_cap + 1));
+    al((void**)&w.scal, sizeof(long long) * 8);
+    al((void**)&w.chan_base, sizeof(int) * (C + 1));
+    al((void**)&w.norm_priv, sizeof(double) * kNormSlots * C * P);
+    al((void**)&w.norm_batch, sizeof(double) * (C * P + 2 * C));
+    al((void**)&w.stat_priv, sizeof(unsigned long long) * kNormSlots * ST_N);
+    al((void**)&w.stats, sizeof(unsigned long long) * ST_N);
+    al((void**)&w.task_counter, sizeof(unsigned int) * 4);
+    if (!ok) {
+        worklist_destroy(h);
+        return fail(WG_E_OOM, "cannot allocate a work list for %lld records", (long long)max_records);
+    }
+    if (cudaMemset(w.scal, 0, sizeof(long long) * 8) != cudaSuccess ||
+        cudaMemset(w.stats, 0, sizeof(unsigned long long) * ST_N) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        worklist_destroy(h);
+        return cuda_fail(cudaGetLastError(), "worklist_create");
+    }
+    *out = h;
+    return WG_OK;
+}
+
+static int check_vis(const Grid& g, const Table& t, const wg_vis_in* in)
+{
+    if (!in) return fail(WG_E_INVALID_ARG, "null vis input");
+    if (in->n_rows < 0) return fail(WG_E_INVALID_ARG, "n_rows must be >= 0");
+    if (in->n_chan != g.n_chan || in->n_pol != g.n_pol)
+        return fail(WG_E_SHAPE, "vis shape (chan %d, pol %d) differs from the grid's (%d, %d)", in->n_chan, in->n_pol, g.n_chan, g.n_pol);
+    if (in->n_rows > 0 && (!in->uvw || !in->freq_hz || !in->vis || !in->weight || !in->flag))
+        return fail(WG_E_INVALID_ARG, "null input array");
+    if (std::fabs(t.du - g.du) > 1e-12 * g.du) return fail(WG_E_SHAPE, "table du %.17g differs from grid du %.17g", t.du, g.du);
+    if (t.max_support > g.n) return fail(WG_E_OOB_SUPPORT, "support %d larger than the grid (%d)", t.max_support, g.n);
+    if ((reinterpret_cast<uintptr_t>(in->vis) & 7)) return fail(WG_E_INVALID_ARG, "vis must be 8-byte aligned");
+    return WG_OK;
+}
+
+int vis_compress(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, int32_t compress, wg_worklist* wh,
+                 void* stream)
+{
+    t_err[0] = 0;
+    if (!gh || !th || !wh) return fail(WG_E_INVALID_ARG, "vis_compress: null handle");
+    int rc = check_vis(gh->g, th->t, in);
+    if (rc != WG_OK) return rc;
+    WorkList& w = wh->w;
+    if (in->n_chan != w.C || in->n_pol != w.P) return fail(WG_E_SHAPE, "work list was created for %d channels, %d pols", w.C, w.P);
+    if (in->n_rows * (int64_t)in->n_chan > w.cap)
+        return fail(WG_E_CAPACITY, "%lld records exceed the work list capacity %lld", (long long)(in->n_rows * (int64_t)in->n_chan), (long long)w.cap);
+    return launch_prep(th->t, gh->g, *in, compress, w, S(stream));
+}
+
+int worklist_stats(const wg_worklist* wh, wg_stats* out, void* stream)
+{
+    if (!wh || !out) return fail(WG_E_INVALID_ARG, "worklist_stats: null argument");
+    const WorkList& w = wh->w;
+    unsigned long long st[ST_N];
+    long long sc[4];
+    WG_CUDA(cudaMemcpyAsync(st, w.stats, sizeof(st), cudaMemcpyDeviceToHost, S(stream)));
+    WG_CUDA(cudaMemcpyAsync(sc, w.scal, sizeof(sc), cudaMemcpyDeviceToHost, S(stream)));
+    WG_CUDA(cudaStreamSynchronize(S(stream)));
+    out->records = (int64_t)st[ST_RECORDS];
+    out->griddable = (int64_t)st[ST_GRIDDABLE];
+    out->gridded = (int64_t)st[ST_GRIDDED];
+    out->compressed = (int64_t)st[ST_COMPRESSED];
+    out->updates = (int64_t)st[ST_UPD] * w.P;
+    out->updates_saved = (int64_t)st[ST_UPD_SAVED] * w.P;
+    out->tasks = (int64_t)st[ST_TASKS];
+    out->dropped = sc[3];
+    return WG_OK;
+}
+
+int worklist_view(const wg_worklist* wh, const int32_t** entries, const void** gamma, const int32_t** runs,
+                  const uint8_t** rec_class, int64_t* n_entries, void* stream)
+{
+    if (!wh) return fail(WG_E_INVALID_ARG, "worklist_view: null work list");
+    const WorkList& w = wh->w;
+    if (entries) *entries = reinterpret_cast<const int32_t*>(w.entries);
+    if (gamma) *gamma = w.gamma;
+    if (runs) *runs = reinterpret_cast<const int32_t*>(w.runs);
+    if (rec_class) *rec_class = w.rclass;
+    if (n_entries) {
+        long long n = 0;
+        WG_CUDA(cudaMemcpyAsync(&n, w.scal, sizeof(n), cudaMemcpyDeviceToHost, S(stream)));
+        WG_CUDA(cudaStreamSynchronize(S(stream)));
+        *n_entries = n;
+    }
+    return WG_OK;
+}
+
+int grid_vis(wg_grid* gh, const wg_table* th, const wg_worklist* wh, void* stream)
+{
+    t_err[0] = 0;
+    if (!gh || !th || !wh) return fail(WG_E_INVALID_ARG, "grid_vis: null handle");
+    Grid& g = gh->g;
+    const WorkList& w = wh->w;
+    if (w.C != g.n_chan || w.P != g.n_pol) return fail(WG_E_SHAPE, "work list shape differs from the grid's");
+    if (w.N != 0 && w.N != g.n) return fail(WG_E_SHAPE, "work list was prepared for N=%d, grid has N=%d", w.N, g.n);
+    return launch_grid(g, th->t, w, S(stream));
+}
+
+int degrid_vis(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, const wg_worklist* wh, int32_t mode,
+               void* vis_out, void* stream)
+{
+    t_err[0] = 0;
+    if (!gh || !th || !wh || !vis_out) return fail(WG_E_INVALID_ARG, "degrid_vis: null argument");
+    if (mode != WG_DEGRID_PREDICT && mode != WG_DEGRID_ADJOINT) return fail(WG_E_INVALID_ARG, "unknown degrid mode %d", mode);
+    int rc = check_vis(gh->g, th->t, in);
+    if (rc != WG_OK) return rc;
+    const WorkList& w = wh->w;
+    if (w.rows != in->n_rows || w.C != in->n_chan) return fail(WG_E_SHAPE, "work list was prepared for a different batch");
+    if (reinterpret_cast<uintptr_t>(vis_out) & 7) return fail(WG_E_INVALID_ARG, "vis_out must be 8-byte aligned");
+    return launch_degrid(gh->g, th->t, *in, w, mode, static_cast<float2*>(vis_out), S(stream));
+}
+
+int grid_correct(wg_grid* gh, const wg_table* th, int32_t mode, float* image_out, void* stream)
+{
+    t_err[0] = 0;
+    if (!gh || !th || !image_out) return fail(WG_E_INVALID_ARG, "grid_correct: null argument");
+    if (mode != WG_IMAGE_PER_POL && mode != WG_IMAGE_STOKES_I) return fail(WG_E_INVALID_ARG, "unknown image mode %d", mode);
+    if (std::fabs(th->t.du - gh->g.du) > 1e-12 * gh->g.du) return fail(WG_E_SHAPE, "table du differs from grid du");
+    return launch_correct(gh->g, th->t, mode, image_out, S(stream));
+}
+
+}  // extern "C"

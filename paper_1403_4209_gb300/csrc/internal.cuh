@@ -1,0 +1,150 @@
+// Internal declarations of the wgrid library (handles, error reporting, kernel launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "wgrid.h"
+
+namespace wg {
+
+// ---- errors -------------------------------------------------------------------------
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+#define WG_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+#define WG_LAUNCHED(what)                                       \
+    do {                                                        \
+        ::wg::count_launch();                                   \
+        cudaError_t e_ = cudaGetLastError();                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);      \
+    } while (0)
+
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int num_sms();
+
+// ---- compile-time limits --------------------------------------------------------------
+constexpr int kMaxSupport = 1023;     // largest odd support
+constexpr int kMaxBeta = 64;
+constexpr int kTileRecords = 2048;    // records per preparation tile (rows x channels)
+constexpr int kSegLen = 128;          // gridded entries per gridder segment
+constexpr int kSlotsPerBlock = 256;   // footprint points per gridder task (32 lanes x 8)
+constexpr int kRMax = 8;              // points per lane
+constexpr int kNormSlots = 256;       // privatised normaliser accumulators
+
+// ---- handles --------------------------------------------------------------------------
+struct Grid {
+    int n = 0, n_pol = 0, n_chan = 0;
+    double du = 0;
+    float2* data = nullptr;
+    bool owns = false;
+    double* norm = nullptr;               // [n_chan][n_pol]
+    unsigned long long* counters = nullptr;  // [8] accumulated statistics
+    // grid_correct resources
+    float2* scratch = nullptr;            // [N][N][P]
+    double* corr = nullptr;               // [N] taper x sinc
+    int corr_s0 = -1, corr_beta = -1;
+    cufftHandle plan = 0;
+    bool plan_ok = false;
+};
+
+struct Table {
+    int K = 0, beta = 0, s0 = 0, max_support = 0;
+    double w_max = 0, du = 0;
+    int64_t n_samples = 0;
+    float2* data = nullptr;               // C-1, complex float32
+    double* zeta = nullptr;               // C-3 [K beta^2]
+    int* supports_d = nullptr;            // C-2 supports [K]
+    int* offsets_d = nullptr;             // C-2 offsets [K]
+    std::vector<int> supports, offsets;   // host copies
+    std::vector<double> pswf;             // Legendre coefficients of psi_0 (even degrees)
+};
+
+struct WorkList {
+    int64_t cap = 0;                      // records
+    int C = 0, P = 0;
+    int64_t tile_cap = 0;                 // tiles x C counters
+    int64_t seg_cap = 0;
+    // per record
+    int4* rinfo = nullptr;
+    uint8_t* rclass = nullptr;
+    // per (tile, chan)
+    int* tile_cnt = nullptr;
+    // per gridded entry (channel-major)
+    int4* entries = nullptr;
+    float2* gamma = nullptr;
+    int2* runs = nullptr;
+    // segments
+    int* seg_nblk = nullptr;
+    int* seg_off = nullptr;               // [seg_cap + 1]
+    // scalars and small arrays (device)
+    long long* scal = nullptr;            // [0] n_entries [1] n_tasks [2] n_seg [3] overflow
+    int* chan_base = nullptr;             // [C + 1]
+    double* norm_priv = nullptr;          // [kNormSlots][C][P]
+    double* norm_batch = nullptr;         // [C][P]
+    unsigned long long* stat_priv = nullptr;  // [kNormSlots][8]
+    unsigned long long* stats = nullptr;  // [8]
+    unsigned int* task_counter = nullptr;
+    // last batch
+    int64_t rows = 0;
+    int rpb = 0;
+    int64_t n_tiles = 0;
+    int N = 0;
+};
+
+// statistics slots
+enum { ST_RECORDS = 0, ST_GRIDDABLE, ST_GRIDDED, ST_COMPRESSED, ST_UPD, ST_UPD_SAVED, ST_TASKS, ST_N };
+
+// rinfo.w bit layout
+constexpr int kBitG = 12, kBitC = 13, kBitNeg = 14, kBitGd = 15;
+
+// ---- launchers (defined in the .cu files) ---------------------------------------------
+struct PlaceParams {
+    int N, beta, K, lo, compress, C, P;
+    double w_max, beta_over_du;
+    const int* supports;
+    const int* offsets;
+    const double* zeta;
+};
+
+int launch_prep(const Table& t, const Grid& g, const wg_vis_in& in, int compress, WorkList& wl,
+                cudaStream_t s);
+int launch_grid(Grid& g, const Table& t, const WorkList& wl, cudaStream_t s);
+int launch_degrid(const Grid& g, const Table& t, const wg_vis_in& in, const WorkList& wl, int mode,
+                  float2* out, cudaStream_t s);
+int launch_correct(Grid& g, const Table& t, int mode, float* image, cudaStream_t s);
+int build_table(const wg_table_desc& d, Table& t, cudaStream_t s);
+int import_table(int K, int beta, double w_max, double du, int s0, const int* supports,
+                 const double* data, const double* zeta, Table& t);
+int free_table(Table& t);
+
+// psi_0(c, x) from its even Legendre coefficients a[0..n): sum_m a_m P_2m(x), by the
+// three-term Legendre recurrence.
+__device__ __forceinline__ double pswf_eval_dev(const double* a, int n, double x)
+{
+    double pm1 = 1.0, p = x, s = a[0];
+    const int deg = 2 * n - 2;
+    for (int j = 1; j < deg; ++j) {
+        const double pn = ((2.0 * j + 1) * x * p - j * pm1) / (j + 1);
+        pm1 = p;
+        p = pn;
+        if ((j + 1) % 2 == 0) s += a[(j + 1) / 2] * p;
+    }
+    return s;
+}
+
+// prolate spheroidal psi_0(c, x) as even Legendre coefficients (host eigen-solver)
+std::vector<double> pswf_coefficients(double c);
+double pswf_eval_host(const std::vector<double>& coef, double x);
+
+}  // namespace wg

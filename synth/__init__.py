@@ -258,7 +258,7 @@ def make(name: str, device: str = "cpu", flag_frac: float = 0.0, n_times: Option
     if n_times is not None or n_baselines is not None:
         # a contiguous block of time steps around transit for the chosen baselines
         t_idx = np.arange(T)[(T - T_used) // 2:(T - T_used) // 2 + T_used]
-        uvw = uvw_full.reshape(-1, T, 3)[: (len(pairs) if n_baselines else None)][:, t_idx]
+        uvw = uvw_full.reshape(-1, T, 3)[:len(pairs)][:, t_idx]
         uvw = np.ascontiguousarray(uvw.reshape(-1, 3))
     else:
         uvw = uvw_full

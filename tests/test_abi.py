@@ -1,0 +1,74 @@
+"""The C-ABI library loads, exports every function include/wgrid.h declares, and rejects bad
+arguments with the documented status codes before touching the GPU (runs without a GPU)."""
+import ctypes
+
+import pytest
+
+import paper_1403_4209_gb300 as wg
+from paper_1403_4209_gb300 import _lib
+
+C = wg.CONST
+
+
+def test_every_declared_symbol_is_exported():
+    names = wg.header_functions()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(wg.lib, n), n
+        assert ctypes.cast(getattr(wg.lib, n), ctypes.c_void_p).value
+
+
+def test_status_codes_distinct():
+    codes = [v for k, v in C.items() if k.startswith("WG_E_")]
+    assert len(set(codes)) == len(codes) and all(c < 0 for c in codes) and C["WG_OK"] == 0
+
+
+def _err():
+    return wg.lib.wg_last_error().decode()
+
+
+@pytest.mark.parametrize("n,pol,chan,du,msg", [(7, 1, 1, 1.0, "even"), (64, 3, 1, 1.0, "n_pol"),
+                                               (64, 1, 0, 1.0, "n_chan"), (64, 1, 1, 0.0, "du")])
+def test_grid_create_rejects(n, pol, chan, du, msg):
+    d = _lib.GridDesc(n, pol, chan, 0, du, None)
+    h = ctypes.c_void_p()
+    assert wg.lib.grid_create(ctypes.byref(d), ctypes.byref(h)) == C["WG_E_INVALID_ARG"]
+    assert msg in _err() and not h.value
+
+
+def _table_desc(supports, K=None, beta=8, mode=None, w_max=0.0):
+    K = K or len(supports)
+    arr = (ctypes.c_int32 * K)(*supports)
+    return _lib.TableDesc(K, beta, 7, 0, C["WG_SUPPORT_PRESCRIBED"] if mode is None else mode, C["WG_F32"],
+                          w_max, 1.0, 1e-3, ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32))), arr
+
+
+def test_table_rejects_even_and_oversized_supports():
+    h = ctypes.c_void_p()
+    d, keep = _table_desc([8])
+    assert wg.lib.conv_table_build(ctypes.byref(d), ctypes.byref(h), None) == C["WG_E_INVALID_ARG"]
+    d, keep = _table_desc([2049])
+    assert wg.lib.conv_table_build(ctypes.byref(d), ctypes.byref(h), None) == C["WG_E_OOB_SUPPORT"]
+    d, keep = _table_desc([7, 9], beta=0)
+    assert wg.lib.conv_table_build(ctypes.byref(d), ctypes.byref(h), None) == C["WG_E_INVALID_ARG"]
+    d, keep = _table_desc([7, 9], w_max=0.0)
+    assert wg.lib.conv_table_build(ctypes.byref(d), ctypes.byref(h), None) == C["WG_E_INVALID_ARG"]
+    assert "w_max" in _err()
+
+
+def test_worklist_and_null_handles():
+    h = ctypes.c_void_p()
+    assert wg.lib.worklist_create(100, 1, 3, ctypes.byref(h)) == C["WG_E_INVALID_ARG"]
+    assert wg.lib.worklist_create(0, 1, 1, ctypes.byref(h)) == C["WG_E_INVALID_ARG"]
+    vi = _lib.VisIn()
+    assert wg.lib.vis_compress(None, None, ctypes.byref(vi), 1, None, None) == C["WG_E_INVALID_ARG"]
+    assert wg.lib.grid_vis(None, None, None, None) == C["WG_E_INVALID_ARG"]
+    assert wg.lib.degrid_vis(None, None, ctypes.byref(vi), None, 0, None, None) == C["WG_E_INVALID_ARG"]
+    assert wg.lib.grid_correct(None, None, 0, None, None) == C["WG_E_INVALID_ARG"]
+    st = _lib.Stats()
+    assert wg.lib.worklist_stats(None, ctypes.byref(st), None) == C["WG_E_INVALID_ARG"]
+
+
+def test_errors_raise_in_python():
+    with pytest.raises(wg.WgError, match="WG_E_INVALID_ARG"):
+        _lib.check(wg.lib.worklist_create(0, 1, 1, ctypes.byref(ctypes.c_void_p())), "worklist_create")
