@@ -19,6 +19,7 @@ roofline = the gridder kernel against the FP32 FMA pipe (8 flops per update, Sec
 same workload (only rank 0 runs it under torchrun).
 """
 import argparse
+import datetime
 import hashlib
 import json
 import math
@@ -54,24 +55,39 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons every 200 ms.  Started (and waited for) before the
+    warm-up so that its start-up never falls inside the timed region; only samples time-stamped
+    inside the timed region are kept."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.t0 = self.t1 = None
         self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
 
-    def start(self):
+    def start(self, wait_s=20.0):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.tmp, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        t = time.time()
+        while time.time() - t < wait_s:
+            if os.path.getsize(self.tmp.name) > 0:
+                break
+            time.sleep(0.1)
+
+    def begin(self):
+        self.t0 = datetime.datetime.now()
+
+    def end(self):
+        self.t1 = datetime.datetime.now()
 
     def stop(self):
         if self.proc is None:
@@ -83,17 +99,32 @@ class ClockSampler:
         with open(self.tmp.name) as f:
             for line in f:
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) < 9:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                except ValueError:
+                    continue
+                rows.append((ts, parts))
         os.unlink(self.tmp.name)
-        if not rows:
+        inside = [p for ts, p in rows if self.t0 and self.t1 and
+                  self.t0 - datetime.timedelta(seconds=0.25) <= ts <= self.t1 + datetime.timedelta(seconds=0.25)]
+        if not inside and rows and self.t1:
+            inside = [min(rows, key=lambda r: abs((r[0] - self.t1).total_seconds()))[1]]
+        if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[1]) for r in inside) if v is not None]
+        mx = [v for v in (num(r[2]) for r in inside) if v is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[5 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(inside)}
 
 
 def _gridder_traffic(per_launch_units):
@@ -149,6 +180,8 @@ def run_ours(args, rank, world, local_rank):
             ev_g[k][1].record(stream)
         wg.grid_correct(g, tab, mode=wg.IMAGE_STOKES_I, out=img)
 
+    clocks = ClockSampler(local_rank)
+    clocks.start()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -156,8 +189,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local_rank)
-    clocks.start()
+    clocks.begin()
     n0 = wg.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -166,6 +198,7 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     launches = wg.launch_count() - n0
+    clocks.end()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     t_grid = sum(a.elapsed_time(b) for a, b in ev_g) / args.steps
