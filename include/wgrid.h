@@ -231,6 +231,36 @@ int degrid_vis(const wg_grid* grid, const wg_table* table, const wg_vis_in* in,
 int grid_correct(wg_grid* grid, const wg_table* table, int32_t mode, float* image_out,
                  void* stream);
 
+/* ---- allocation-free gridding of small batches ---------------------------------------
+ * The thesis has no counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc: code recording into a CUDA graph (an allocation breaks the capture), processes
+ * whose device memory belongs to another allocator or to a fixed budget, and real-time
+ * loops that must stay out of the driver's allocator.  It does what vis_compress followed by
+ * grid_vis does, without a work list: its scratch is a fixed 6 MB array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   - At most WG_NOALLOC_MAX_RECORDS records (n_rows * n_chan) and WG_NOALLOC_MAX_CHAN
+ *     channels per call; larger batches return WG_E_CAPACITY (split them into calls).
+ *   - The first call on each device looks up the scratch's device address for that device
+ *     (with it current) and caches it: make the first call before any stream capture.
+ *   - Every call reuses the same scratch and clears what must start at zero itself; calls
+ *     whose GPU work overlaps (several streams or host threads at once) race on it, so
+ *     serialise them.
+ *   - The caller passes the output grid and normaliser as device pointers (layouts as for
+ *     grid_create); both are accumulated into.  `table` comes from conv_table_build or
+ *     conv_table_import.  Nothing is allocated or freed: no cudaMalloc, no cudaFree. */
+#define WG_NOALLOC_MAX_RECORDS 65536
+#define WG_NOALLOC_MAX_CHAN 64
+
+typedef struct wg_grid_view {
+    int32_t n, n_pol, n_chan, reserved; /* as wg_grid_desc                                */
+    double du;                          /* cell size in wavelengths                      */
+    void* data;                         /* device complex64 [n_chan][N][N][n_pol], 16-B aligned */
+    double* normaliser;                 /* device double [n_chan][n_pol]                  */
+} wg_grid_view;
+
+int grid_vis_noalloc(const wg_grid_view* grid, const wg_table* table, const wg_vis_in* in,
+                     int32_t compress, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

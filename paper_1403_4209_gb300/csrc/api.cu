@@ -7,10 +7,6 @@
 
 #include "internal.cuh"
 
-struct wg_grid { wg::Grid g; };
-struct wg_table { wg::Table t; };
-struct wg_worklist { wg::WorkList w; };
-
 namespace wg {
 
 std::atomic<uint64_t> g_launches{0};

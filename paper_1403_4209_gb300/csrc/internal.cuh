@@ -148,3 +148,8 @@ std::vector<double> pswf_coefficients(double c);
 double pswf_eval_host(const std::vector<double>& coef, double x);
 
 }  // namespace wg
+
+// opaque C-ABI handles
+struct wg_grid { wg::Grid g; };
+struct wg_table { wg::Table t; };
+struct wg_worklist { wg::WorkList w; };
