@@ -138,7 +138,7 @@ def _gridder_traffic(per_launch_units):
     with open(prof) as f:
         for line in f:
             if ":" in line and line.startswith("- "):
-                k, v = line[2:].split(":", 1)
+                k, v = line[2:].rsplit(":", 1)
                 kv[k.strip()] = v.strip().strip("`")
     try:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
