@@ -3,23 +3,87 @@
 // Work unit ("task") = one segment of kSegLen consecutive gridded entries x one block of up to
 // kSlotsPerBlock footprint points.  A warp takes tasks from a global counter (persistent
 // kernel, dynamic load balance).  Each lane owns R <= kRMax fixed residue classes
-// (x mod S, y mod S) of the footprint, the ownership Romein's algorithm uses (Sec. 2.5): for
+// (x mod S, y mod S) of the footprint, the ownership of Romein's algorithm (Sec. 2.5): for
 // every record exactly one grid pixel of each owned class lies inside the S x S footprint, so
-// lanes never touch the same pixel and can accumulate in registers while the pixel stays the
-// same; when it moves, the lane flushes its accumulators to the grid with one vector FP32
-// atomic per pixel (all polarisations of a pixel are contiguous).  Records are staged per warp
-// in shared memory, 32 at a time; kernel samples are read through the read-only cache.  A
-// change of support or channel inside a segment flushes and re-maps the lane's classes.
+// lanes never touch the same pixel and accumulate in registers while the pixel stays the
+// same; when it moves, the lane flushes its accumulators with one vector FP32 atomic per pixel
+// (all polarisations of a pixel are contiguous).
+//
+// Fast path: consecutive gridded entries of a track usually keep the same footprint origin and
+// differ only in the sub-kernel z (about 85% of them, weighted by S^2, in the benchmark
+// workload).  Then each point's kernel offset toff = dv S + du and pixel are unchanged: the lane
+// only loads C[z + toff] and does 4P FMAs, and the next record's samples are prefetched into
+// registers while the current record's FMAs run.  When the footprint moves, the lane recomputes
+// its offsets with the modular wrap and flushes the pixels that changed.  The segment's entries
+// and weighted visibilities are staged in shared memory once per task (cp.async).  R (points per
+// lane) is a template parameter, dispatched per run of records with the same support and channel.
 #include "internal.cuh"
 
 namespace wg {
 
 namespace {
 
+constexpr int kWarps = 4;           // warps per block
+
 template <int P>
-__device__ __forceinline__ void flush_pixel(float2* __restrict__ gch, int pix, float2 (&a)[P])
+struct WarpSmem {
+    int4 e[kSegLen];
+    float2 g[kSegLen * P];
+    int puv[kRMax][32];   // each lane's owned residue classes (pu | pv << 16), slow path only
+    int cur[kRMax][32];   // each lane's current pixels, slow path only
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Packed FP32 pairs (Blackwell f32x2 arithmetic): one instruction does two FP32 FMAs.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pack2(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ float2 unpack2(f32x2 v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+template <int P>
+__device__ __forceinline__ void flush_pixel(float2* __restrict__ gch, int pix, f32x2 (&acc)[P])
 {
     float2* d = gch + (size_t)pix * P;
+    float2 a[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) a[p] = unpack2(acc[p]);
     if constexpr (P == 1) {
         atomicAdd(d, a[0]);
     } else if constexpr (P == 2) {
@@ -29,22 +93,136 @@ __device__ __forceinline__ void flush_pixel(float2* __restrict__ gch, int pix, f
         atomicAdd(reinterpret_cast<float4*>(d + 2), make_float4(a[2].x, a[2].y, a[3].x, a[3].y));
     }
 #pragma unroll
-    for (int p = 0; p < P; ++p) a[p] = make_float2(0.f, 0.f);
+    for (int p = 0; p < P; ++p) acc[p] = 0ull;
+}
+
+// After staging, an entry's w field holds its key: support << 16 | channel, or -1 for an
+// entry rejected by the staging bounds checks.
+__device__ __forceinline__ int entry_key(const int4& E) { return E.w; }
+
+// Processes records [j, e1) while their (support, channel) key equals `key` with R <= kRMax
+// points per lane (task block `blk` of the support's footprint); flushes its pixels and returns
+// the first record not processed.  R is warp-uniform: the unrolled point loops stop at R.
+template <int P>
+__device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R, int blk, int N, int lane,
+                                           WarpSmem<P>& sm, const float2* __restrict__ table,
+                                           const int* __restrict__ supports, float2* __restrict__ gch)
+{
+    f32x2 acc[kRMax][P];
+    int toff[kRMax];
+    unsigned valid = 0;
+    const int s2 = S * S, sbase = blk * 32 * R;
+#pragma unroll
+    for (int r = 0; r < kRMax; ++r) {
+        const int sl = sbase + r * 32 + lane;
+        sm.cur[r][lane] = -1;
+        toff[r] = 0;
+        if (r < R && sl < s2) {
+            valid |= 1u << r;
+            const int pv = sl / S;
+            sm.puv[r][lane] = (sl - pv * S) | (pv << 16);
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) acc[r][p] = 0ull;
+    }
+    int fp = -1;             // footprint origin (x0 | y0 << 16) the offsets refer to
+    bool pre = false;        // the current buffer holds the current record's samples (prefetched)
+    float2 kva[kRMax], kvb[kRMax];
+    // One record: load its samples unless prefetched, prefetch the next record's into `nxt` when
+    // it keeps the footprint, then accumulate.  Returns false when the run ends at record j.
+    auto step = [&](float2 (&cur_kv)[kRMax], float2 (&nxt)[kRMax]) -> bool {
+        if (j >= e1) return false;
+        const int4 E = sm.e[j];
+        if (entry_key(E) != key) return false;
+        if (!pre) {
+            if (E.x != fp) {     // the footprint moved: new offsets, flush the pixels that change
+                const int x0 = E.x & 0xFFFF, y0 = (E.x >> 16) & 0xFFFF;
+                const int cu = E.y & 0xFFFF, cv = (E.y >> 16) & 0xFFFF;
+#pragma unroll
+                for (int r = 0; r < kRMax; ++r) {
+                    if (r < R && (valid & (1u << r))) {
+                        const int puv = sm.puv[r][lane];
+                        int du = (puv & 0xFFFF) + cu;
+                        du -= (du >= S) ? S : 0;
+                        int dv = (puv >> 16) + cv;
+                        dv -= (dv >= S) ? S : 0;
+                        toff[r] = dv * S + du;
+                        const int pix = (y0 + dv) * N + x0 + du;
+                        const int cur = sm.cur[r][lane];
+                        if (pix != cur) {
+                            if (cur >= 0) flush_pixel<P>(gch, cur, acc[r]);
+                            sm.cur[r][lane] = pix;
+                        }
+                    }
+                }
+                fp = E.x;
+            }
+            const float2* kz = table + E.z;
+#pragma unroll
+            for (int r = 0; r < kRMax; ++r) {
+                if (r >= R) break;
+                cur_kv[r] = __ldg(kz + toff[r]);   // invalid points read offset 0, never flushed
+            }
+        }
+        pre = false;
+        if (j + 1 < e1) {
+            const int4 E1 = sm.e[j + 1];
+            if (E1.x == fp && entry_key(E1) == key) {
+                const float2* kz = table + E1.z;
+#pragma unroll
+                for (int r = 0; r < kRMax; ++r) {
+                    if (r >= R) break;
+                    nxt[r] = __ldg(kz + toff[r]);
+                }
+                pre = true;
+            }
+        }
+        // acc += gamma * kv as (gx, gy) (kx, kx) + (-gy, gx) (ky, ky), two packed FMAs per pol
+        f32x2 g1[P], g2[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float2 gm = sm.g[j * P + p];
+            g1[p] = pack2(gm.x, gm.y);
+            g2[p] = pack2(-gm.y, gm.x);
+        }
+#pragma unroll
+        for (int r = 0; r < kRMax; ++r) {
+            if (r >= R) break;
+            const f32x2 kxx = pack2(cur_kv[r].x, cur_kv[r].x), kyy = pack2(cur_kv[r].y, cur_kv[r].y);
+#pragma unroll
+            for (int p = 0; p < P; ++p) acc[r][p] = fma2(g2[p], kyy, fma2(g1[p], kxx, acc[r][p]));
+        }
+        ++j;
+        return true;
+    };
+    for (;;) {
+        if (!step(kva, kvb)) break;
+        if (!step(kvb, kva)) break;
+    }
+#pragma unroll
+    for (int r = 0; r < kRMax; ++r) {
+        const int cur = sm.cur[r][lane];
+        if (cur >= 0) flush_pixel<P>(gch, cur, acc[r]);
+    }
+    return j;
 }
 
 }  // namespace
 
 template <int P>
-__global__ void __launch_bounds__(256, 2) k_grid(const int4* __restrict__ entries, const float2* __restrict__ gamma,
-                                                 const int* __restrict__ seg_off, const long long* __restrict__ scal,
-                                                 const int* __restrict__ supports, const float2* __restrict__ table,
-                                                 float2* __restrict__ grid, int N, int K, int C, int64_t n_samples,
-                                                 unsigned int* __restrict__ counter, long long* __restrict__ dropped)
+__global__ void __launch_bounds__(kWarps * 32, 4) k_grid(const int4* __restrict__ entries,
+                                                         const float2* __restrict__ gamma,
+                                                         const int* __restrict__ seg_off,
+                                                         const long long* __restrict__ scal,
+                                                         const int* __restrict__ supports,
+                                                         const float2* __restrict__ table,
+                                                         float2* __restrict__ grid, int N, int K, int C,
+                                                         int64_t n_samples, unsigned int* __restrict__ counter,
+                                                         long long* __restrict__ dropped)
 {
-    constexpr int W = 8;
-    __shared__ int4 s_e[W][32];
-    __shared__ float2 s_g[W][32 * P];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    WarpSmem<P>& sm = reinterpret_cast<WarpSmem<P>*>(smem_raw)[wid];
     const long long n_entries = scal[0], n_tasks = scal[1], n_seg = scal[2];
     const size_t chan_stride = (size_t)N * N * P;
 
@@ -60,104 +238,61 @@ __global__ void __launch_bounds__(256, 2) k_grid(const int4* __restrict__ entrie
         }
         const int blk = (int)t - __ldg(&seg_off[lo]);
         const int e0 = lo * kSegLen;
-        const int e1 = (int)min((long long)e0 + kSegLen, n_entries);
+        const int n = (int)min((long long)kSegLen, n_entries - e0);
 
-        int curS = -1, curCh = -1;
-        bool active = false;
-        unsigned valid = 0;
-        int pu[kRMax], pv[kRMax], cur[kRMax];
-        float2 acc[kRMax][P];
+        // stage the segment's entries and weighted visibilities
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            cp_async16(&sm.e[i], entries + e0 + i);
+            if constexpr (P == 1) {
+                cp_async8(&sm.g[i], gamma + (size_t)(e0 + i));
+            } else {
 #pragma unroll
-        for (int r = 0; r < kRMax; ++r) {
-            cur[r] = -1;
-            pu[r] = pv[r] = 0;
-#pragma unroll
-            for (int p = 0; p < P; ++p) acc[r][p] = make_float2(0.f, 0.f);
-        }
-        float2* gch = grid;
-
-        for (int base = e0; base < e1; base += 32) {
-            const int n = min(32, e1 - base);
-            __syncwarp();
-            if (lane < n) {
-                s_e[wid][lane] = entries[base + lane];
-#pragma unroll
-                for (int p = 0; p < P; ++p) s_g[wid][lane * P + p] = gamma[(size_t)(base + lane) * P + p];
+                for (int p = 0; p < P; p += 2) cp_async16(&sm.g[i * P + p], gamma + (size_t)(e0 + i) * P + p);
             }
-            __syncwarp();
-            for (int j = 0; j < n; ++j) {
-                const int4 E = s_e[wid][j];
-                const int k = E.w & 0xFFF, ch = (E.w >> 16) & 0xFFFF;
-                if (k >= K || ch >= C) {          // device-side bounds check (never taken)
-                    if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
-                    continue;
-                }
+        }
+        cp_commit();
+        cp_wait<0>();
+        __syncwarp();
+        // device-side bounds checks (never taken with a consistent work list)
+        for (int i = lane; i < n; i += 32) {
+            const int4 E = sm.e[i];
+            const int k = E.w & 0xFFF, ch = (E.w >> 16) & 0xFFFF;
+            bool ok = E.w >= 0 && k < K && ch < C;
+            if (ok) {
                 const int S = __ldg(&supports[k]);
-                {
-                    const int x0c = E.x & 0xFFFF, y0c = (E.x >> 16) & 0xFFFF;
-                    if (x0c + S > N || y0c + S > N || E.z < 0 || (int64_t)E.z + (int64_t)S * S > n_samples) {
-                        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
-                        continue;
-                    }
-                }
-                if (S != curS || ch != curCh) {
-#pragma unroll
-                    for (int r = 0; r < kRMax; ++r)
-                        if (cur[r] >= 0) {
-                            flush_pixel<P>(gch, cur[r], acc[r]);
-                            cur[r] = -1;
-                        }
-                    curS = S;
-                    curCh = ch;
-                    gch = grid + (size_t)ch * chan_stride;
-                    const int s2 = S * S;
-                    const int nb = (s2 + kSlotsPerBlock - 1) / kSlotsPerBlock;
-                    active = blk < nb;
-                    const int R = (s2 + 32 * nb - 1) / (32 * nb);
-                    const int sbase = blk * 32 * R;
-                    valid = 0;
-#pragma unroll
-                    for (int r = 0; r < kRMax; ++r) {
-                        const int sl = sbase + r * 32 + lane;
-                        if (r < R && sl < s2) {
-                            valid |= 1u << r;
-                            pv[r] = sl / S;
-                            pu[r] = sl - pv[r] * S;
-                        }
-                    }
-                }
-                if (!active) continue;
                 const int x0 = E.x & 0xFFFF, y0 = (E.x >> 16) & 0xFFFF;
                 const int cu = E.y & 0xFFFF, cv = (E.y >> 16) & 0xFFFF;
-                const int z = E.z;
-                float2 gm[P];
-#pragma unroll
-                for (int p = 0; p < P; ++p) gm[p] = s_g[wid][j * P + p];
-#pragma unroll
-                for (int r = 0; r < kRMax; ++r) {
-                    if (valid & (1u << r)) {
-                        int du = pu[r] + cu;
-                        du -= (du >= S) ? S : 0;
-                        int dv = pv[r] + cv;
-                        dv -= (dv >= S) ? S : 0;
-                        const int pix = (y0 + dv) * N + x0 + du;
-                        const float2 kv = __ldg(&table[z + dv * S + du]);
-                        if (pix != cur[r]) {
-                            if (cur[r] >= 0) flush_pixel<P>(gch, cur[r], acc[r]);
-                            cur[r] = pix;
-                        }
-#pragma unroll
-                        for (int p = 0; p < P; ++p) {
-                            acc[r][p].x = fmaf(gm[p].x, kv.x, fmaf(-gm[p].y, kv.y, acc[r][p].x));
-                            acc[r][p].y = fmaf(gm[p].x, kv.y, fmaf(gm[p].y, kv.x, acc[r][p].y));
-                        }
-                    }
-                }
+                ok = x0 + S <= N && y0 + S <= N && cu < S && cv < S && E.z >= 0 &&
+                     (int64_t)E.z + (int64_t)S * S <= n_samples;
+            }
+            if (ok) {
+                sm.e[i].w = (__ldg(&supports[k]) << 16) | ch;
+            } else {
+                sm.e[i].w = -1;
+                if (blk == 0) atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
             }
         }
-#pragma unroll
-        for (int r = 0; r < kRMax; ++r)
-            if (cur[r] >= 0) flush_pixel<P>(gch, cur[r], acc[r]);
+        __syncwarp();
+
+        int j = 0;
+        while (j < n) {
+            const int key = entry_key(sm.e[j]);
+            if (key < 0) {
+                ++j;
+                continue;
+            }
+            const int S = key >> 16, ch = key & 0xFFFF;
+            float2* gch = grid + (size_t)ch * chan_stride;
+            const int s2 = S * S;
+            const int nb = (s2 + kSlotsPerBlock - 1) / kSlotsPerBlock;
+            const int R = (s2 + 32 * nb - 1) / (32 * nb);
+            if (blk >= nb) {     // this block has no points for this support: skip the run
+                while (j < n && entry_key(sm.e[j]) == key) ++j;
+                continue;
+            }
+            j = run_records<P>(j, n, key, S, R, blk, N, lane, sm, table, supports, gch);
+        }
     }
 }
 
@@ -174,15 +309,17 @@ template <int P>
 static int grid_impl(Grid& g, const Table& t, const WorkList& wl, cudaStream_t s)
 {
     static int blocks_per_sm = 0;
+    const int smem = (int)(kWarps * sizeof(WarpSmem<P>));
     if (blocks_per_sm == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_grid<P>, 256, 0) != cudaSuccess ||
+        WG_CUDA(cudaFuncSetAttribute(k_grid<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_grid<P>, kWarps * 32, smem) != cudaSuccess ||
             blocks_per_sm < 1)
             blocks_per_sm = 1;
     }
     WG_CUDA(cudaMemsetAsync(wl.task_counter, 0, sizeof(unsigned int), s));
-    k_grid<P><<<num_sms() * blocks_per_sm, 256, 0, s>>>(wl.entries, wl.gamma, wl.seg_off, wl.scal, t.supports_d,
-                                                         t.data, g.data, g.n, t.K, g.n_chan, t.n_samples,
-                                                         wl.task_counter, wl.scal + 3);
+    k_grid<P><<<num_sms() * blocks_per_sm, kWarps * 32, smem, s>>>(wl.entries, wl.gamma, wl.seg_off, wl.scal,
+                                                                   t.supports_d, t.data, g.data, g.n, t.K, g.n_chan,
+                                                                   t.n_samples, wl.task_counter, wl.scal + 3);
     WG_LAUNCHED("k_grid");
     const int n = g.n_chan * g.n_pol;
     const int m = std::max(n, (int)ST_N);
