@@ -12,7 +12,10 @@ position tuple; Sec. 4.3.4 eq. "conj"), written as plain FP64 steps, each rounde
   x_c     = ceil((q - beta/2) / beta)  (integer arithmetic), frac = q - beta x_c
             in (-beta/2, beta/2]
   x       = N/2 + x_c                (u = 0 in the middle of the grid, Sec. 4.3.3)
-  k       = floor((K-1) * sqrt(w / w_max) + 0.5)   nearest plane in sqrt(w)
+  k       = number of m in 1..K-1 with w >= b_m, where b_m = w_max * (t_m * t_m),
+            t_m = (m - 0.5) / (K - 1): the squared midpoints between planes in sqrt(w), so k is
+            the nearest plane in sqrt(w) (Sec. 2.2.1 / 4.2.1), ties upward; w >= b_K is beyond
+            the last plane by more than half a spacing and not griddable
   S = S_k, h = (S-1)/2, footprint origin (x0, y0) = (x - h, y - h)
   z       = offset_k + ((frac_v - lo) * beta + (frac_u - lo)) * S^2,  lo = -((beta-1)//2)
 
@@ -44,6 +47,15 @@ class Placement:
     zeta_idx: np.ndarray # index into C-3 (-1 where not griddable)
     griddable: np.ndarray  # bool
     chan: np.ndarray     # int32 channel of each record
+
+
+def plane_bounds(K: int, w_max: float) -> np.ndarray:
+    """b_m = w_max * (t * t), t = (m - 0.5) / (K - 1), for m = 1..K (FP64, each op rounded once)."""
+    out = np.empty(K)
+    for m in range(1, K + 1):
+        t = (m - 0.5) / (K - 1)
+        out[m - 1] = w_max * (t * t)
+    return out
 
 
 def _cell(q: np.ndarray, beta: int):
@@ -80,12 +92,15 @@ def place(uvw_m: np.ndarray, freq_hz: np.ndarray, du: float, n_grid: int, table,
     y = n_grid // 2 + yc
     if K == 1:
         k = np.zeros_like(x)
+        inplane = sane
     else:
         if not table.w_max > 0.0:
             raise ValueError("w_max must be positive with more than one w-plane")
-        k = np.floor((K - 1) * np.sqrt(w / table.w_max) + 0.5)
-        k = np.where(np.isfinite(k) & (k < 2.0 ** 30), k, 2.0 ** 30).astype(np.int64)
-    inplane = (k <= K - 1) & sane
+        b = plane_bounds(K, table.w_max)                     # b_1 .. b_K
+        k = np.zeros(w.shape, dtype=np.int64)
+        for m in range(1, K):
+            k += (w >= b[m - 1])
+        inplane = (w < b[K - 1]) & sane
     kc = np.where(inplane, k, 0)
     S = np.where(inplane, table.supports[kc], 0).astype(np.int64)
     h = (S - 1) // 2

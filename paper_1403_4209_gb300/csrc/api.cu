@@ -101,6 +101,8 @@ int grid_destroy(wg_grid* h)
     cudaFree(g.counters);
     cudaFree(g.scratch);
     cudaFree(g.corr);
+    cudaFree(g.icorr);
+    cudaFree(g.inv_norm);
     if (g.plan_ok) cufftDestroy(g.plan);
     delete h;
     return WG_OK;

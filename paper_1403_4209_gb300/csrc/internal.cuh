@@ -51,8 +51,11 @@ struct Grid {
     double* norm = nullptr;               // [n_chan][n_pol]
     unsigned long long* counters = nullptr;  // [8] accumulated statistics
     // grid_correct resources
-    float2* scratch = nullptr;            // [N][N][P]
+    float2* scratch = nullptr;            // [G][N][N][P], G = scratch_chans
+    int scratch_chans = 0;
     double* corr = nullptr;               // [N] taper x sinc
+    float* icorr = nullptr;               // [N] 1 / (taper x sinc)
+    float* inv_norm = nullptr;            // [n_chan][n_pol] 1 / N_p (0 where N_p = 0)
     int corr_s0 = -1, corr_beta = -1;
     cufftHandle plan = 0;
     bool plan_ok = false;
@@ -66,6 +69,8 @@ struct Table {
     double* zeta = nullptr;               // C-3 [K beta^2]
     int* supports_d = nullptr;            // C-2 supports [K]
     int* offsets_d = nullptr;             // C-2 offsets [K]
+    double* wbounds_d = nullptr;          // [K] squared sqrt(w) midpoints between planes
+    float* zeta_f = nullptr;              // C-3 in FP32 (normaliser terms)
     std::vector<int> supports, offsets;   // host copies
     std::vector<double> pswf;             // Legendre coefficients of psi_0 (even degrees)
 };
@@ -114,7 +119,8 @@ struct PlaceParams {
     double w_max, beta_over_du;
     const int* supports;
     const int* offsets;
-    const double* zeta;
+    const double* wbounds;
+    const float* zeta_f;
 };
 
 int launch_prep(const Table& t, const Grid& g, const wg_vis_in& in, int compress, WorkList& wl,

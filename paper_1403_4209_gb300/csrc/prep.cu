@@ -59,11 +59,14 @@ __device__ __forceinline__ Placed place(const double* __restrict__ uvw, int64_t 
     const long long xc = floor_div(2 * iqu + b - 1, 2 * b), yc = floor_div(2 * iqv + b - 1, 2 * b);
     const int fu = (int)(iqu - b * xc), fv = (int)(iqv - b * yc);
     int k = 0;
-    if (pp.K > 1) {
-        const double r = __dsqrt_rn(__ddiv_rn(w, pp.w_max));
-        const double t = floor(__dadd_rn(__dmul_rn((double)(pp.K - 1), r), 0.5));
-        if (!(t <= (double)(pp.K - 1))) return o;
-        k = (int)t;
+    if (pp.K > 1) {   // nearest plane in sqrt(w): k = number of b_1..b_{K-1} with w >= b_m
+        if (!(w < __ldg(&pp.wbounds[pp.K - 1]))) return o;   // beyond the last plane (or NaN)
+        int lo = 0, hi = pp.K - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (w >= __ldg(&pp.wbounds[mid - 1])) lo = mid; else hi = mid - 1;
+        }
+        k = lo;
     }
     const int S = __ldg(&pp.supports[k]);
     const int h = (S - 1) / 2;
@@ -199,11 +202,11 @@ __global__ void __launch_bounds__(512) k_classify(const double* __restrict__ uvw
             u_g += g ? s2 : 0ull;
             u_c += c ? s2 : 0ull;
             const int sub = (info.z - __ldg(&pp.offsets[k])) / (S * S);
-            const double zeta = __ldg(&pp.zeta[k * pp.beta * pp.beta + sub]);
+            const float zeta = __ldg(&pp.zeta_f[k * pp.beta * pp.beta + sub]);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 const float wf = weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
-                atomicAdd(&s_norm[ch * P + p], (float)(wf * zeta));
+                atomicAdd(&s_norm[ch * P + p], wf * zeta);
             }
         }
     }
@@ -443,7 +446,8 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int com
     pp.beta_over_du = (double)t.beta / g.du;
     pp.supports = t.supports_d;
     pp.offsets = t.offsets_d;
-    pp.zeta = t.zeta;
+    pp.wbounds = t.wbounds_d;
+    pp.zeta_f = t.zeta_f;
 
     double* lam_inv = reinterpret_cast<double*>(wl.norm_batch + (size_t)C * P);   // [C]
     double* sc = lam_inv + C;                                                     // [C]

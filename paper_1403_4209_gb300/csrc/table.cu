@@ -148,9 +148,13 @@ int free_table(Table& t)
     cudaFree(t.zeta);
     cudaFree(t.supports_d);
     cudaFree(t.offsets_d);
+    cudaFree(t.wbounds_d);
+    cudaFree(t.zeta_f);
     t.data = nullptr;
     t.zeta = nullptr;
     t.supports_d = t.offsets_d = nullptr;
+    t.wbounds_d = nullptr;
+    t.zeta_f = nullptr;
     return WG_OK;
 }
 
@@ -169,14 +173,31 @@ static int finish_layout(Table& t)
     if (cudaMalloc(&t.data, sizeof(float2) * std::max<int64_t>(off, 1)) != cudaSuccess ||
         cudaMalloc(&t.zeta, sizeof(double) * t.K * t.beta * t.beta) != cudaSuccess ||
         cudaMalloc(&t.supports_d, sizeof(int) * t.K) != cudaSuccess ||
-        cudaMalloc(&t.offsets_d, sizeof(int) * t.K) != cudaSuccess) {
+        cudaMalloc(&t.offsets_d, sizeof(int) * t.K) != cudaSuccess ||
+        cudaMalloc(&t.wbounds_d, sizeof(double) * t.K) != cudaSuccess ||
+        cudaMalloc(&t.zeta_f, sizeof(float) * t.K * t.beta * t.beta) != cudaSuccess) {
         cudaGetLastError();
         free_table(t);
         return fail(WG_E_OOM, "cannot allocate the kernel table (%lld samples)", (long long)off);
     }
     WG_CUDA(cudaMemcpy(t.supports_d, t.supports.data(), sizeof(int) * t.K, cudaMemcpyHostToDevice));
     WG_CUDA(cudaMemcpy(t.offsets_d, t.offsets.data(), sizeof(int) * t.K, cudaMemcpyHostToDevice));
+    // nearest plane in sqrt(w): plane k is chosen when b_k <= w < b_{k+1}, with
+    // b_m = w_max (t t), t = (m - 1/2) / (K - 1), m = 1..K (b_K bounds the last plane)
+    std::vector<double> wb(t.K, 0.0);
+    if (t.K > 1)
+        for (int m = 1; m <= t.K; ++m) {
+            const double tm = (m - 0.5) / (double)(t.K - 1);
+            wb[m - 1] = t.w_max * (tm * tm);
+        }
+    WG_CUDA(cudaMemcpy(t.wbounds_d, wb.data(), sizeof(double) * t.K, cudaMemcpyHostToDevice));
     return WG_OK;
+}
+
+__global__ void k_zeta_f32(const double* __restrict__ z, int n, float* __restrict__ zf)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) zf[i] = (float)z[i];
 }
 
 int build_table(const wg_table_desc& d, Table& t, cudaStream_t s)
@@ -272,6 +293,11 @@ int build_table(const wg_table_desc& d, Table& t, cudaStream_t s)
             count_launch();
         }
         if (rc != WG_OK) break;
+        {
+            const int nz = K * beta * beta;
+            k_zeta_f32<<<(nz + 255) / 256, 256, 0, s>>>(t.zeta, nz, t.zeta_f);
+            count_launch();
+        }
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_fail(e, "conv_table_build");
     } while (0);
@@ -298,8 +324,11 @@ int import_table(int K, int beta, double w_max, double du, int s0, const int* su
     if (rc != WG_OK) return rc;
     std::vector<float2> h((size_t)t.n_samples);
     for (int64_t i = 0; i < t.n_samples; ++i) h[i] = make_float2((float)data[2 * i], (float)data[2 * i + 1]);
+    std::vector<float> zf((size_t)K * beta * beta);
+    for (size_t i = 0; i < zf.size(); ++i) zf[i] = (float)zeta[i];
     if (cudaMemcpy(t.data, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(t.zeta, zeta, sizeof(double) * K * beta * beta, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(t.zeta, zeta, sizeof(double) * K * beta * beta, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t.zeta_f, zf.data(), sizeof(float) * zf.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
         free_table(t);
         return fail(WG_E_CUDA, "table upload failed");
     }

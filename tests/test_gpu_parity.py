@@ -113,3 +113,21 @@ def test_accumulates_over_batches():
     assert rel_l2(g.data.cpu().numpy(), 2 * gp["grid"]) < 1e-6
     # per-tile partial sums of N_p are FP32 atomics: order-dependent at ~1e-7
     assert max_rel(g.normaliser().cpu().numpy(), 2 * gp["norm"]) < 1e-6
+
+
+def test_plane_boundaries_bit_exact():
+    # w exactly on each squared sqrt(w) midpoint b_m and one ulp either side (f = c0, so w' is w
+    # in wavelengths): the plane index and griddability must match the oracle bit for bit
+    from oracle.place import plane_bounds
+    K, w_max = 7, 500.0
+    b = plane_bounds(K, w_max)
+    ws = np.concatenate([[0.0], b, np.nextafter(b, np.inf), np.nextafter(b, -np.inf), -b])
+    rows = ws.size
+    rng = np.random.default_rng(3)
+    uvw = np.stack([rng.uniform(-20, 20, rows), rng.uniform(-20, 20, rows), ws], 1)
+    wl = synth.Workload("plane_edges", uvw, np.array([synth.C0]), torch.ones((rows, 1, 1), dtype=torch.complex64),
+                        torch.ones((rows, 1, 1)), torch.zeros((rows, 1, 1), dtype=torch.uint8), 256, 1.0, K,
+                        w_max, 4, [9, 9, 11, 11, 13, 13, 15], 7, rows, 1)
+    gp, o = _check(wl, False)
+    pl = o["pl"]
+    assert not pl.griddable[1 + K - 1] and pl.griddable[1 + 3 * K - 1]   # b_K excluded, just below it included
