@@ -60,9 +60,21 @@ extern "C" {
 #define WG_DEGRID_PREDICT 0 /* model visibilities: psi-conjugated kernel sums          */
 #define WG_DEGRID_ADJOINT 1 /* exact adjoint of the vis -> grid map (also eps (1-f))   */
 
+/* vis_compress flags (bit set) */
+#define WG_PREP_COMPRESS 1   /* compress consecutive records (Sec. 4.3.3)                */
+#define WG_PREP_UNWEIGHTED 2 /* gamma and N_p use weight 1 and ignore per-pol flags; the */
+                             /* griddable records are unchanged (all-flagged ones stay   */
+                             /* excluded): gridding is then the adjoint of PREDICT-mode  */
+                             /* degridding                                               */
+
 /* grid_correct modes */
 #define WG_IMAGE_PER_POL 0 /* output float [n_chan][n_pol][N][N]                      */
 #define WG_IMAGE_STOKES_I 1 /* output float [n_chan][N][N]: mean of pols 0 and P-1     */
+#define WG_IMAGE_PER_POL_RAW 2 /* as PER_POL without the division by N_p               */
+#define WG_IMAGE_TRANSPOSE 3 /* reads image_out (float [n_chan][n_pol][N][N]) and      */
+                             /* OVERWRITES the grid with the exact transpose of mode 2:  */
+                             /* grid = (-1)^(x+y) FFT((-1)^(mx+my) img / (taper sinc)),  */
+                             /* the sky-to-grid half of the forward model               */
 
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* wg_last_error(void);
@@ -185,18 +197,18 @@ typedef struct wg_stats {
  *      footprint origin (x - (S_k-1)/2, y - (S_k-1)/2); kernel pointer
  *      z = offset_k + ((frac_v - lo) beta + (frac_u - lo)) S_k^2, lo = -((beta-1)/2)
  *      griddable: k <= K-1, footprint inside the grid, some polarisation unflagged;
- *   A2 compression (if `compress` != 0): record (r, c) is compressed into (r-1, c) when
+ *   A2 compression (if flags & WG_PREP_COMPRESS): record (r, c) is compressed into (r-1, c) when
  *      both are griddable with equal footprint origin and z (eq. "ci");
  *   A3 compaction of gridded records into channel-major lists, segmented into tasks;
  *   A4 gamma = sum over each run of eps (1-f) psi-conj(vis) (eqs. "compress1",
- *      "conjugatetake"), FP32;
+ *      "conjugatetake"), FP32 (eps (1-f) = 1 with WG_PREP_UNWEIGHTED);
  *   A5 the normaliser terms and statistics, added into the grid's N_p and counters when
  *      grid_vis runs.
  * `grid` supplies N and du; `table` the planes, supports and zeta.  The work list keeps
  * the results until the next call on it.
  * Errors: INVALID_ARG, SHAPE (n_chan/n_pol/du mismatch), CAPACITY, CUDA. */
 int vis_compress(const wg_grid* grid, const wg_table* table, const wg_vis_in* in,
-                 int32_t compress, wg_worklist* wl, void* stream);
+                 int32_t flags, wg_worklist* wl, void* stream);
 
 /* Copies the work list's statistics (Sec. 4.3.4) to *out.  Synchronises `stream`. */
 int worklist_stats(const wg_worklist* wl, wg_stats* out, void* stream);
@@ -226,7 +238,8 @@ int degrid_vis(const wg_grid* grid, const wg_table* table, const wg_vis_in* in,
 /* A9, Algorithm "finalizer": inverse FFT per polarisation (cuFFT, FP32, centred so that
  * image pixel N/2 is l = 0), real part, divide by N_p, by the taper psi_0(c, 2 du l)
  * psi_0(c, 2 du m) and by sinc(pi l du / beta) sinc(pi m du / beta), l = (k - N/2)/(N du).
- * image_out: device float, layout per `mode`.  The grid is not modified.
+ * image_out: device float, layout per `mode`.  The grid is not modified, except by
+ * WG_IMAGE_TRANSPOSE, which reads image_out and writes the grid (see the mode list).
  * Errors: INVALID_ARG, SHAPE, CUDA. */
 int grid_correct(wg_grid* grid, const wg_table* table, int32_t mode, float* image_out,
                  void* stream);

@@ -21,6 +21,9 @@ steps of its Algorithm "convgen" in order, in FP64:
   grid.degrid         adjoint of the gridding map (not in the thesis)
   correct.grid_correct  Algorithm "finalizer" steps 1-4 (Sec. 4.7)
   dft.dirty_image     direct Fourier inversion including the w-term (Sec. 1.4 / 2.2.1)
+  model.forward / model.adjoint / model.chi2_grad
+                      sky -> visibility forward model from degridding, its adjoint and the
+                      chi^2 gradient (not in the thesis)
 
 Parity pins (tests/test_oracle_*.py) tie each of these to something other than itself:
 closed forms, brute force, invariants and worked counts from the thesis.  Parity
@@ -34,6 +37,7 @@ from .place import place, classify, Placement
 from .grid import grid_plain, grid_compressed, compress, normaliser, stats, degrid, weighted_vis
 from .correct import grid_correct, taper_1d
 from .dft import dirty_image
+from . import model
 
 __all__ = [
     "psi0", "Table", "build_table", "delta_table", "place", "classify", "Placement",

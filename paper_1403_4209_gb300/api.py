@@ -20,6 +20,10 @@ DEGRID_PREDICT = CONST["WG_DEGRID_PREDICT"]
 DEGRID_ADJOINT = CONST["WG_DEGRID_ADJOINT"]
 IMAGE_PER_POL = CONST["WG_IMAGE_PER_POL"]
 IMAGE_STOKES_I = CONST["WG_IMAGE_STOKES_I"]
+IMAGE_PER_POL_RAW = CONST["WG_IMAGE_PER_POL_RAW"]
+IMAGE_TRANSPOSE = CONST["WG_IMAGE_TRANSPOSE"]
+PREP_COMPRESS = CONST["WG_PREP_COMPRESS"]
+PREP_UNWEIGHTED = CONST["WG_PREP_UNWEIGHTED"]
 
 
 def _stream(stream=None):
@@ -209,8 +213,9 @@ class WorkList:
 
 
 def vis_compress(grid: Grid, table: ConvTable, batch: VisBatch, worklist: WorkList, compress: bool = True,
-                 stream=None):
-    check(lib.vis_compress(grid.handle, table.handle, ctypes.byref(batch.struct), int(bool(compress)),
+                 unweighted: bool = False, stream=None):
+    flags = (PREP_COMPRESS if compress else 0) | (PREP_UNWEIGHTED if unweighted else 0)
+    check(lib.vis_compress(grid.handle, table.handle, ctypes.byref(batch.struct), flags,
                            worklist.handle, _stream(stream)), "vis_compress")
 
 
@@ -231,7 +236,9 @@ def degrid_vis(grid: Grid, table: ConvTable, batch: VisBatch, worklist: WorkList
 
 def grid_correct(grid: Grid, table: ConvTable, mode: int = IMAGE_PER_POL, out: torch.Tensor = None,
                  stream=None) -> torch.Tensor:
-    shape = (grid.n_chan, grid.n_pol, grid.n, grid.n) if mode == IMAGE_PER_POL else (grid.n_chan, grid.n, grid.n)
+    if mode == IMAGE_TRANSPOSE:
+        raise ValueError("use image_to_grid for the transpose mode")
+    shape = (grid.n_chan, grid.n, grid.n) if mode == IMAGE_STOKES_I else (grid.n_chan, grid.n_pol, grid.n, grid.n)
     if out is None:
         out = torch.empty(shape, dtype=torch.float32, device=grid.data.device)
     if out.dtype != torch.float32 or tuple(out.shape) != shape or not out.is_contiguous():
@@ -239,3 +246,14 @@ def grid_correct(grid: Grid, table: ConvTable, mode: int = IMAGE_PER_POL, out: t
     check(lib.grid_correct(grid.handle, table.handle, int(mode), c_vp(out.data_ptr()), _stream(stream)),
           "grid_correct")
     return out
+
+
+def image_to_grid(grid: Grid, table: ConvTable, image: torch.Tensor, stream=None) -> Grid:
+    """Overwrites grid with the transpose of grid_correct(mode=IMAGE_PER_POL_RAW) applied to a
+    float32 [n_chan][n_pol][N][N] image: the sky-to-grid half of the forward model."""
+    shape = (grid.n_chan, grid.n_pol, grid.n, grid.n)
+    if image.dtype != torch.float32 or tuple(image.shape) != shape or not image.is_contiguous() or not image.is_cuda:
+        raise ValueError("image must be a contiguous CUDA float32 tensor of shape %s" % (shape,))
+    check(lib.grid_correct(grid.handle, table.handle, IMAGE_TRANSPOSE, c_vp(image.data_ptr()), _stream(stream)),
+          "grid_correct")
+    return grid

@@ -299,7 +299,7 @@ static int check_vis(const Grid& g, const Table& t, const wg_vis_in* in)
     return WG_OK;
 }
 
-int vis_compress(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, int32_t compress, wg_worklist* wh,
+int vis_compress(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, int32_t flags, wg_worklist* wh,
                  void* stream)
 {
     t_err[0] = 0;
@@ -310,7 +310,8 @@ int vis_compress(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, int
     if (in->n_chan != w.C || in->n_pol != w.P) return fail(WG_E_SHAPE, "work list was created for %d channels, %d pols", w.C, w.P);
     if (in->n_rows * (int64_t)in->n_chan > w.cap)
         return fail(WG_E_CAPACITY, "%lld records exceed the work list capacity %lld", (long long)(in->n_rows * (int64_t)in->n_chan), (long long)w.cap);
-    return launch_prep(th->t, gh->g, *in, compress, w, S(stream));
+    if (flags & ~(WG_PREP_COMPRESS | WG_PREP_UNWEIGHTED)) return fail(WG_E_INVALID_ARG, "unknown vis_compress flags %d", flags);
+    return launch_prep(th->t, gh->g, *in, flags, w, S(stream));
 }
 
 int worklist_stats(const wg_worklist* wh, wg_stats* out, void* stream)
@@ -380,7 +381,7 @@ int grid_correct(wg_grid* gh, const wg_table* th, int32_t mode, float* image_out
 {
     t_err[0] = 0;
     if (!gh || !th || !image_out) return fail(WG_E_INVALID_ARG, "grid_correct: null argument");
-    if (mode != WG_IMAGE_PER_POL && mode != WG_IMAGE_STOKES_I) return fail(WG_E_INVALID_ARG, "unknown image mode %d", mode);
+    if (mode < WG_IMAGE_PER_POL || mode > WG_IMAGE_TRANSPOSE) return fail(WG_E_INVALID_ARG, "unknown image mode %d", mode);
     if (std::fabs(th->t.du - gh->g.du) > 1e-12 * gh->g.du) return fail(WG_E_SHAPE, "table du differs from grid du");
     return launch_correct(gh->g, th->t, mode, image_out, S(stream));
 }

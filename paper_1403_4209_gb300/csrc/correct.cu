@@ -11,6 +11,9 @@
 //      pi (k - N/2) / (N beta).
 // The divisions are multiplications by reciprocals prepared once in FP64 and applied in FP32.
 // A polarisation whose normaliser is zero (no data) gives a zero image.
+// WG_IMAGE_PER_POL_RAW skips the division by N_p; WG_IMAGE_TRANSPOSE applies the exact transpose
+// of that map (the adjoint of Re(inverse FFT) under the real inner product is the forward FFT of
+// the real image): grid = (-1)^(x+y) FFT_forward((-1)^(mx+my) img / (taper sinc)).
 #include "internal.cuh"
 
 namespace wg {
@@ -57,13 +60,26 @@ __global__ void k_finish(const float2* __restrict__ f, int N, int P, int64_t npi
     const int my = (int)(pix / N), mx = (int)(pix - (int64_t)my * N);
     const float cc = ((mx + my) & 1 ? -1.f : 1.f) * icorr[mx] * icorr[my];
     const float2* fp = f + q * P;
-    const float* in = inv_norm + gch * P;
-    if (mode == WG_IMAGE_PER_POL) {
-        for (int p = 0; p < P; ++p) img[(gch * P + p) * nn + pix] = fp[p].x * in[p] * cc;
+    const float* in = inv_norm ? inv_norm + gch * P : nullptr;
+    if (mode == WG_IMAGE_PER_POL || mode == WG_IMAGE_PER_POL_RAW) {
+        for (int p = 0; p < P; ++p) img[(gch * P + p) * nn + pix] = fp[p].x * (in ? in[p] : 1.f) * cc;
     } else {
         const float v0 = fp[0].x * in[0] * cc;
         img[gch * nn + pix] = (P == 1) ? v0 : 0.5f * (v0 + fp[P - 1].x * in[P - 1] * cc);
     }
+}
+
+// transpose, step 1: scratch = (-1)^(mx+my) img / (taper sinc) as complex, per group of channels
+__global__ void k_image_in(const float* __restrict__ img, int N, int P, int64_t npix, const float* __restrict__ icorr,
+                           float2* __restrict__ f)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= npix) return;
+    const int64_t nn = (int64_t)N * N;
+    const int64_t gch = q / nn, pix = q - gch * nn;
+    const int my = (int)(pix / N), mx = (int)(pix - (int64_t)my * N);
+    const float cc = ((mx + my) & 1 ? -1.f : 1.f) * icorr[mx] * icorr[my];
+    for (int p = 0; p < P; ++p) f[q * P + p] = make_float2(img[(gch * P + p) * nn + pix] * cc, 0.f);
 }
 
 int launch_correct(Grid& g, const Table& t, int mode, float* image, cudaStream_t s)
@@ -103,10 +119,27 @@ int launch_correct(Grid& g, const Table& t, int mode, float* image, cudaStream_t
         g.corr_beta = t.beta;
     }
     if (cufftSetStream(g.plan, s) != CUFFT_SUCCESS) return fail(WG_E_CUDA, "cufftSetStream failed");
-    k_inv_norm<<<(C * P + 127) / 128, 128, 0, s>>>(g.norm, C * P, g.inv_norm);
-    WG_LAUNCHED("k_inv_norm");
-    const size_t img_stride = (mode == WG_IMAGE_PER_POL) ? (size_t)P * N * N : (size_t)N * N;
     const int64_t tot = (int64_t)G * per_chan, npix = (int64_t)G * N * N;
+    if (mode == WG_IMAGE_TRANSPOSE) {
+        for (int c0 = 0; c0 < C; c0 += G) {
+            k_image_in<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(image + (size_t)c0 * P * N * N, N, P, npix,
+                                                                      g.icorr, g.scratch);
+            WG_LAUNCHED("k_image_in");
+            for (int p = 0; p < P; ++p) {
+                cufftComplex* d = reinterpret_cast<cufftComplex*>(g.scratch + p);
+                if (cufftExecC2C(g.plan, d, d, CUFFT_FORWARD) != CUFFT_SUCCESS) return fail(WG_E_CUDA, "cufftExecC2C failed");
+            }
+            k_modulate<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g.scratch, g.data + (size_t)c0 * per_chan, N, P, tot);
+            WG_LAUNCHED("k_modulate");
+        }
+        return WG_OK;
+    }
+    const bool raw = (mode == WG_IMAGE_PER_POL_RAW);
+    if (!raw) {
+        k_inv_norm<<<(C * P + 127) / 128, 128, 0, s>>>(g.norm, C * P, g.inv_norm);
+        WG_LAUNCHED("k_inv_norm");
+    }
+    const size_t img_stride = (mode == WG_IMAGE_STOKES_I) ? (size_t)N * N : (size_t)P * N * N;
     for (int c0 = 0; c0 < C; c0 += G) {
         k_modulate<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g.data + (size_t)c0 * per_chan, g.scratch, N, P, tot);
         WG_LAUNCHED("k_modulate");
@@ -115,8 +148,9 @@ int launch_correct(Grid& g, const Table& t, int mode, float* image, cudaStream_t
             cufftComplex* d = reinterpret_cast<cufftComplex*>(g.scratch + p);
             if (cufftExecC2C(g.plan, d, d, CUFFT_INVERSE) != CUFFT_SUCCESS) return fail(WG_E_CUDA, "cufftExecC2C failed");
         }
-        k_finish<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(g.scratch, N, P, npix, g.icorr, g.inv_norm + (size_t)c0 * P,
-                                                                mode, image + (size_t)c0 * img_stride);
+        k_finish<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(g.scratch, N, P, npix, g.icorr,
+                                                                raw ? nullptr : g.inv_norm + (size_t)c0 * P, mode,
+                                                                image + (size_t)c0 * img_stride);
         WG_LAUNCHED("k_finish");
     }
     return WG_OK;

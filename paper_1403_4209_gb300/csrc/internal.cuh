@@ -115,7 +115,7 @@ constexpr int kBitG = 12, kBitC = 13, kBitNeg = 14, kBitGd = 15;
 
 // ---- launchers (defined in the .cu files) ---------------------------------------------
 struct PlaceParams {
-    int N, beta, K, lo, compress, C, P;
+    int N, beta, K, lo, compress, unweighted, C, P;
     double w_max, beta_over_du;
     const int* supports;
     const int* offsets;
@@ -123,7 +123,7 @@ struct PlaceParams {
     const float* zeta_f;
 };
 
-int launch_prep(const Table& t, const Grid& g, const wg_vis_in& in, int compress, WorkList& wl,
+int launch_prep(const Table& t, const Grid& g, const wg_vis_in& in, int flags, WorkList& wl,
                 cudaStream_t s);
 int launch_grid(Grid& g, const Table& t, const WorkList& wl, cudaStream_t s);
 int launch_degrid(const Grid& g, const Table& t, const wg_vis_in& in, const WorkList& wl, int mode,

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(512) k_classify(const double* __restrict__ uvw
             const float zeta = __ldg(&pp.zeta_f[k * pp.beta * pp.beta + sub]);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const float wf = weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
+                const float wf = pp.unweighted ? 1.0f : weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
                 atomicAdd(&s_norm[ch * P + p], wf * zeta);
             }
         }
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
                                                  const int* __restrict__ chan_base, const int* __restrict__ supports,
                                                  int4* __restrict__ entries, float2* __restrict__ gamma,
                                                  int2* __restrict__ runs, int* __restrict__ seg_nblk, int64_t cap,
-                                                 long long* __restrict__ scal)
+                                                 long long* __restrict__ scal, int unweighted)
 {
     const int64_t tile = blockIdx.x;
     const int64_t row0 = tile * rpb;
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
             const float sg = ((info.w >> kBitNeg) & 1) ? -1.f : 1.f;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const float wf = weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
+                const float wf = unweighted ? 1.0f : weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
                 const float2 v = vis[rec * P + p];
                 acc[p] = make_float2(wf * v.x, sg * (wf * v.y));
             }
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
             const float sg = ((i2.w >> kBitNeg) & 1) ? -1.f : 1.f;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const float wf = weight[rc2 * P + p] * (1.0f - (float)flag[rc2 * P + p]);
+                const float wf = unweighted ? 1.0f : weight[rc2 * P + p] * (1.0f - (float)flag[rc2 * P + p]);
                 const float2 v = vis[rc2 * P + p];
                 acc[p].x += wf * v.x;
                 acc[p].y += sg * (wf * v.y);
@@ -421,7 +421,7 @@ static size_t classify_smem(int rpb, int C, int P)
 }
 
 template <int P>
-static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int compress, WorkList& wl,
+static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int flags, WorkList& wl,
                      cudaStream_t s)
 {
     const int C = in.n_chan;
@@ -439,7 +439,8 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int com
     pp.beta = t.beta;
     pp.K = t.K;
     pp.lo = -((t.beta - 1) / 2);
-    pp.compress = compress ? 1 : 0;
+    pp.compress = (flags & WG_PREP_COMPRESS) ? 1 : 0;
+    pp.unweighted = (flags & WG_PREP_UNWEIGHTED) ? 1 : 0;
     pp.C = C;
     pp.P = P;
     pp.w_max = t.w_max;
@@ -474,7 +475,8 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int com
     if (rows > 0) {
         k_compact<P><<<(unsigned)n_tiles, 512, 0, s>>>(wl.rinfo, reinterpret_cast<const float2*>(in.vis), in.weight,
                                                         in.flag, rows, rpb, C, wl.tile_cnt, wl.chan_base, t.supports_d,
-                                                        wl.entries, wl.gamma, wl.runs, wl.seg_nblk, wl.cap, wl.scal);
+                                                        wl.entries, wl.gamma, wl.runs, wl.seg_nblk, wl.cap, wl.scal,
+                                                        pp.unweighted);
         WG_LAUNCHED("k_compact");
     }
     k_seg_scan<<<1, 1024, 0, s>>>(wl.seg_nblk, wl.seg_off, wl.scal, wl.stats);
@@ -482,12 +484,12 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int com
     return WG_OK;
 }
 
-int launch_prep(const Table& t, const Grid& g, const wg_vis_in& in, int compress, WorkList& wl, cudaStream_t s)
+int launch_prep(const Table& t, const Grid& g, const wg_vis_in& in, int flags, WorkList& wl, cudaStream_t s)
 {
     switch (in.n_pol) {
-        case 1: return prep_impl<1>(t, g, in, compress, wl, s);
-        case 2: return prep_impl<2>(t, g, in, compress, wl, s);
-        case 4: return prep_impl<4>(t, g, in, compress, wl, s);
+        case 1: return prep_impl<1>(t, g, in, flags, wl, s);
+        case 2: return prep_impl<2>(t, g, in, flags, wl, s);
+        case 4: return prep_impl<4>(t, g, in, flags, wl, s);
         default: return fail(WG_E_INVALID_ARG, "n_pol must be 1, 2 or 4 (got %d)", in.n_pol);
     }
 }
