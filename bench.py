@@ -211,6 +211,39 @@ def run_ours(args, rank, world, local_rank):
     total = st["updates"] + st["updates_saved"]
     value = world * total / (ms * 1e-3) / 1e9
 
+    # precision variants (reduced-precision tables, half visibilities, compensated flushes)
+    variants = {}
+    if not args.no_variants:
+        vis_h, scale_h = synth.to_half_vis(wl.vis)
+        batch_h = wg.VisBatch(uvw_d, freq_d, vis_h, wl.weight, wl.flag, vis_scale=scale_h)
+        for name, store, half, comp in (("fp32+compensated", "f32", False, True), ("f16 table", "f16", False, False),
+                                        ("bf16 table", "bf16", False, False), ("f16 vis", "f32", True, False),
+                                        ("f16 table+f16 vis+compensated", "f16", True, True)):
+            tv = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support,
+                                    supports=wl.supports, store=store)
+            gv = wg.Grid(wl.n_grid, wl.du, wl.n_pol, wl.n_chan, device=dev, compensated=comp)
+            bv = batch_h if half else batch
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            nv = 5
+            for it in range(3 + nv):
+                if it == 3:
+                    evs[0].record(stream)
+                gv.zero()
+                wg.vis_compress(gv, tv, bv, wlst, compress=compress)
+                if it == 3 + nv - 1:
+                    evs[2].record(stream)
+                wg.grid_vis(gv, tv, wlst)
+                if it == 3 + nv - 1:
+                    evs[3].record(stream)
+                wg.grid_correct(gv, tv, mode=wg.IMAGE_STOKES_I, out=img)
+            evs[1].record(stream)
+            torch.cuda.synchronize()
+            ms_v = evs[0].elapsed_time(evs[1]) / nv
+            variants[name] = {"ms_per_step": round(ms_v, 3), "gridder_ms": round(evs[2].elapsed_time(evs[3]), 3),
+                              "value": round(total / (ms_v * 1e-3) / 1e9, 1)}
+            del tv, gv
+        del batch_h, vis_h
+
     # degridding of the same batch (predict mode), timed separately
     out_v = torch.empty_like(wl.vis)
     for _ in range(2):
@@ -294,6 +327,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak_source": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flops x %.0f MHz (%s sm_max_mhz)"
                                     % (props.multi_processor_count, sm_mhz, src),
                      "traffic": traffic},
+        "variants": variants,
         "e2e": {"value": round(world * total / (ms_e2e * 1e-3) / 1e9, 3), "unit": "G grid-point updates/s",
                 "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
@@ -387,6 +421,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wproj_2k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip timing the precision variants")
     ap.add_argument("--n-chan", type=int, default=None, help="run a slice: first n channels (profiling)")
     ap.add_argument("--n-times", type=int, default=None, help="run a slice: n time steps (profiling)")
     args = ap.parse_args()

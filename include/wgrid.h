@@ -46,10 +46,20 @@ extern "C" {
 #define WG_E_OOM (-5)         /* device allocation failed                              */
 #define WG_E_CAPACITY (-6)    /* input larger than the worklist was created for        */
 
-/* element types */
-#define WG_F32 0  /* kernel table stored as complex float32                        */
-#define WG_BF16 1 /* kernel table stored as complex bfloat16 (reserved)            */
-#define WG_F16 2  /* kernel table stored as complex float16 (reserved)             */
+/* kernel-table storage read by the gridder (the complex float32 table is always kept too,
+ * for degridding and inspection) */
+#define WG_F32 0  /* complex float32, 8 bytes per sample                            */
+#define WG_BF16 1 /* complex bfloat16, 4 bytes per sample (round to nearest even)    */
+#define WG_F16 2  /* complex float16, 4 bytes per sample (round to nearest even)     */
+
+/* visibility element types (wg_vis_in.vis_dtype) */
+#define WG_VIS_COMPLEX64 0   /* float re, float im                                      */
+#define WG_VIS_COMPLEX_HALF 1 /* float16 re, float16 im; value = vis_scale[chan] x (re, im) */
+
+/* grid flags (wg_grid_desc.flags) */
+#define WG_GRID_COMPENSATED 1 /* flushes recover each atomic add's rounding error     */
+                              /* (TwoSum) into an error grid folded back after every  */
+                              /* grid_vis: an FP32 grid with compensated summation    */
 
 /* support modes of conv_table_build */
 #define WG_SUPPORT_THRESHOLD 0  /* outermost sample with |C| > threshold (Sec. 4.2.3) */
@@ -90,7 +100,7 @@ typedef struct wg_grid_desc {
     int32_t n;      /* grid side N, even, 8 <= N <= 32768                                */
     int32_t n_pol;  /* polarisations per pixel: 1, 2 or 4                                */
     int32_t n_chan; /* channels (independent grids), >= 1                                */
-    int32_t reserved;
+    int32_t flags;  /* 0 or WG_GRID_COMPENSATED (allocates an error grid of the same size)  */
     double du;      /* cell size Delta u = Delta v in wavelengths, > 0                    */
     void* data;     /* optional caller-owned device buffer of n_chan*N*N*n_pol complex64 */
                     /* (8-byte aligned); NULL: the library allocates and owns it          */
@@ -116,7 +126,7 @@ typedef struct wg_table_desc {
     int32_t n_k;           /* image-plane patch side N_k (even, >= 8); 0 = max(64, next    */
                            /* power of two >= 2 * largest support) or 256 (threshold mode) */
     int32_t support_mode;  /* WG_SUPPORT_THRESHOLD or WG_SUPPORT_PRESCRIBED               */
-    int32_t store_dtype;   /* WG_F32                                                      */
+    int32_t store_dtype;   /* WG_F32, WG_BF16 or WG_F16: samples the gridder reads        */
     double w_max;          /* largest |w| in wavelengths (> 0 if K > 1)                    */
     double du;             /* cell size in wavelengths; must equal the grid's              */
     double threshold;      /* support threshold on |C| (thesis: 1e-3)                      */
@@ -141,6 +151,10 @@ int conv_table_import(int32_t n_wplanes, int32_t oversample, double w_max, doubl
                       const double* zeta, wg_table** out);
 int table_destroy(wg_table* table);
 
+/* Sets the storage the gridder reads (WG_F32, WG_BF16, WG_F16), converting the float32 samples
+ * with round-to-nearest-even.  Synchronises the device.  Errors: INVALID_ARG, OOM, CUDA. */
+int table_set_store(wg_table* table, int32_t store_dtype);
+
 typedef struct wg_table_info {
     int32_t n_wplanes, oversample, taper_support, max_support;
     int64_t n_samples;        /* total complex samples in C-1                         */
@@ -149,6 +163,9 @@ typedef struct wg_table_info {
     const double* zeta;       /* device double [K beta^2]                              */
     const int32_t* supports;  /* device int32 [K]                                      */
     const int32_t* offsets;   /* device int32 [K] first sample of each plane           */
+    int32_t store_dtype;      /* storage read by the gridder                           */
+    int32_t reserved;
+    const void* data_lp;      /* device complex bf16/f16 [n_samples], or NULL for WG_F32 */
 } wg_table_info;
 int table_info(const wg_table* table, wg_table_info* info);
 /* Copies C-1 (complex float32, interleaved), C-3 and C-2 to host buffers sized from
@@ -163,9 +180,13 @@ typedef struct wg_vis_in {
     int32_t n_pol;          /* must equal the grid's                                       */
     const double* uvw;      /* device [n_rows][3] baseline in metres (I-1)                */
     const double* freq_hz;  /* device [n_chan] channel frequencies (I-2: lambda^-1 = f/c) */
-    const void* vis;        /* device [n_rows][n_chan][n_pol] complex64 (I-5)             */
+    const void* vis;        /* device [n_rows][n_chan][n_pol] visibilities (I-5), type per */
+                            /* vis_dtype (4-byte aligned for half, 8-byte for complex64)   */
     const float* weight;    /* device [n_rows][n_chan][n_pol] natural weights (I-3)       */
     const uint8_t* flag;    /* device [n_rows][n_chan][n_pol], 1 = flagged (I-4)          */
+    int32_t vis_dtype;      /* WG_VIS_COMPLEX64 (vis is complex64) or WG_VIS_COMPLEX_HALF */
+    int32_t reserved;
+    const float* vis_scale; /* device [n_chan] scales for WG_VIS_COMPLEX_HALF, else NULL  */
 } wg_vis_in;
 
 /* ---- work list: the preparation phase's outputs (Sec. 4.3.4) ----------------------- */

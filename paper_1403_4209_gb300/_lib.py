@@ -16,7 +16,7 @@ c_i32, c_i64, c_u64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint
 
 
 class GridDesc(ctypes.Structure):
-    _fields_ = [("n", c_i32), ("n_pol", c_i32), ("n_chan", c_i32), ("reserved", c_i32),
+    _fields_ = [("n", c_i32), ("n_pol", c_i32), ("n_chan", c_i32), ("flags", c_i32),
                 ("du", c_dbl), ("data", c_vp)]
 
 
@@ -29,12 +29,14 @@ class TableDesc(ctypes.Structure):
 class TableInfo(ctypes.Structure):
     _fields_ = [("n_wplanes", c_i32), ("oversample", c_i32), ("taper_support", c_i32), ("max_support", c_i32),
                 ("n_samples", c_i64), ("w_max", c_dbl), ("du", c_dbl), ("data", c_vp), ("zeta", c_vp),
-                ("supports", c_vp), ("offsets", c_vp)]
+                ("supports", c_vp), ("offsets", c_vp), ("store_dtype", c_i32), ("reserved", c_i32),
+                ("data_lp", c_vp)]
 
 
 class VisIn(ctypes.Structure):
     _fields_ = [("n_rows", c_i64), ("n_chan", c_i32), ("n_pol", c_i32), ("uvw", c_vp), ("freq_hz", c_vp),
-                ("vis", c_vp), ("weight", c_vp), ("flag", c_vp)]
+                ("vis", c_vp), ("weight", c_vp), ("flag", c_vp), ("vis_dtype", c_i32), ("reserved", c_i32),
+                ("vis_scale", c_vp)]
 
 
 class Stats(ctypes.Structure):
@@ -78,6 +80,7 @@ def _load():
         "conv_table_build": (c_i32, [P(TableDesc), P(c_vp), c_vp]),
         "conv_table_import": (c_i32, [c_i32, c_i32, c_dbl, c_dbl, c_i32, P(c_i32), P(c_dbl), P(c_dbl), P(c_vp)]),
         "table_destroy": (c_i32, [c_vp]),
+        "table_set_store": (c_i32, [c_vp, c_i32]),
         "table_info": (c_i32, [c_vp, P(TableInfo)]),
         "table_copy_to_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
         "worklist_create": (c_i32, [c_i64, c_i32, c_i32, P(c_vp)]),

@@ -54,10 +54,12 @@ def launch_count() -> int:
 class Grid:
     """Complex64 uv-grids [n_chan][N][N][n_pol] (torch tensor `data`) plus FP64 normalisers."""
 
-    def __init__(self, n: int, du: float, n_pol: int = 1, n_chan: int = 1, device=None):
+    def __init__(self, n: int, du: float, n_pol: int = 1, n_chan: int = 1, device=None, compensated: bool = False):
+        """compensated: flushes recover each atomic add's rounding error (WG_GRID_COMPENSATED)."""
         self.n, self.du, self.n_pol, self.n_chan = int(n), float(du), int(n_pol), int(n_chan)
         self.data = torch.zeros((n_chan, n, n, n_pol), dtype=torch.complex64, device=device or "cuda")
-        d = GridDesc(self.n, self.n_pol, self.n_chan, 0, self.du, self.data.data_ptr())
+        d = GridDesc(self.n, self.n_pol, self.n_chan, CONST["WG_GRID_COMPENSATED"] if compensated else 0, self.du,
+                     self.data.data_ptr())
         h = c_vp()
         check(lib.grid_create(ctypes.byref(d), ctypes.byref(h)), "grid_create")
         self._h = h
@@ -101,20 +103,24 @@ class ConvTable:
         check(lib.table_copy_to_host(self._h, None, None, sup.ctypes.data, off.ctypes.data), "table_copy_to_host")
         self.supports, self.offsets = sup, off
         self._info = info
+        self.store = {v: k for k, v in self.STORES.items()}[info.store_dtype]
 
     @property
     def handle(self):
         return self._h
 
+    STORES = {"f32": CONST["WG_F32"], "bf16": CONST["WG_BF16"], "f16": CONST["WG_F16"]}
+
     @classmethod
     def build(cls, du: float, n_wplanes: int = 1, w_max: float = 0.0, oversample: int = 8,
-              taper_support: int = 7, supports=None, n_k: int = 0, threshold: float = 1e-3, stream=None):
+              taper_support: int = 7, supports=None, n_k: int = 0, threshold: float = 1e-3, store: str = "f32",
+              stream=None):
         sup_arr = None
         if supports is not None:
             sup_arr = (ctypes.c_int32 * n_wplanes)(*[int(s) for s in supports])
         d = TableDesc(int(n_wplanes), int(oversample), int(taper_support), int(n_k),
                       SUPPORT_PRESCRIBED if supports is not None else SUPPORT_THRESHOLD,
-                      CONST["WG_F32"], float(w_max), float(du), float(threshold),
+                      cls.STORES[store], float(w_max), float(du), float(threshold),
                       ctypes.cast(sup_arr, ctypes.POINTER(ctypes.c_int32)) if sup_arr is not None else None)
         h = c_vp()
         check(lib.conv_table_build(ctypes.byref(d), ctypes.byref(h), _stream(stream)), "conv_table_build")
@@ -134,6 +140,17 @@ class ConvTable:
               "conv_table_import")
         return cls(h)
 
+    def set_store(self, store: str):
+        """Storage the gridder reads: "f32", "bf16" or "f16" (round to nearest even)."""
+        check(lib.table_set_store(self._h, self.STORES[store]), "table_set_store")
+        self.store = store
+
+    def lp_samples(self) -> torch.Tensor:
+        """The low-precision copy as a device int32 view (one complex bf16/f16 pair per element)."""
+        info = TableInfo()
+        check(lib.table_info(self._h, ctypes.byref(info)), "table_info")
+        return _view(info.data_lp, (int(info.n_samples),), "<i4")
+
     def to_host(self):
         """(C-1 complex64 numpy, zeta float64, supports int32, offsets int32)."""
         data = np.zeros(self.n_samples, np.complex64)
@@ -150,9 +167,10 @@ class ConvTable:
 
 class VisBatch:
     """Device inputs I-1..I-5 (Sec. 4.3.2): uvw [rows,3] f64 metres, freq [C] f64 Hz, vis
-    [rows,C,P] complex64, weight [rows,C,P] f32, flag [rows,C,P] uint8."""
+    [rows,C,P] complex64 (or complex32 = two float16 with per-channel float32 scales
+    `vis_scale` [C]: value = scale x vis), weight [rows,C,P] f32, flag [rows,C,P] uint8."""
 
-    def __init__(self, uvw, freq, vis, weight, flag):
+    def __init__(self, uvw, freq, vis, weight, flag, vis_scale=None):
         def dev(t, dtype):
             t = torch.as_tensor(t)
             if t.dtype != dtype:
@@ -162,7 +180,11 @@ class VisBatch:
             return t.contiguous()
         self.uvw = dev(uvw, torch.float64)
         self.freq = dev(freq, torch.float64)
-        self.vis = dev(vis, torch.complex64)
+        half = torch.as_tensor(vis).dtype == torch.complex32
+        self.vis = dev(vis, torch.complex32 if half else torch.complex64)
+        self.vis_scale = dev(vis_scale, torch.float32) if half else None
+        if half and (self.vis_scale is None or self.vis_scale.shape != (self.vis.shape[1],)):
+            raise ValueError("half-precision visibilities need vis_scale of shape [n_chan]")
         self.weight = dev(weight, torch.float32)
         self.flag = dev(flag, torch.uint8)
         rows, C, P = self.vis.shape
@@ -171,7 +193,9 @@ class VisBatch:
             raise ValueError("inconsistent input shapes")
         self.rows, self.n_chan, self.n_pol = rows, C, P
         self.struct = VisIn(rows, C, P, self.uvw.data_ptr(), self.freq.data_ptr(), self.vis.data_ptr(),
-                            self.weight.data_ptr(), self.flag.data_ptr())
+                            self.weight.data_ptr(), self.flag.data_ptr(),
+                            CONST["WG_VIS_COMPLEX_HALF"] if half else CONST["WG_VIS_COMPLEX64"], 0,
+                            self.vis_scale.data_ptr() if half else None)
 
 
 class WorkList:

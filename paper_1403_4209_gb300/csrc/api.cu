@@ -58,6 +58,7 @@ int grid_create(const wg_grid_desc* d, wg_grid** out)
     if (d->n_chan < 1 || d->n_chan > 4096) return fail(WG_E_INVALID_ARG, "n_chan=%d must be in [1, 4096]", d->n_chan);
     if (!(d->du > 0.0)) return fail(WG_E_INVALID_ARG, "cell size du must be positive");
     if (d->data && (reinterpret_cast<uintptr_t>(d->data) & 15)) return fail(WG_E_INVALID_ARG, "external grid buffer must be 16-byte aligned");
+    if (d->flags & ~WG_GRID_COMPENSATED) return fail(WG_E_INVALID_ARG, "unknown grid flags %d", d->flags);
     wg_grid* h = new (std::nothrow) wg_grid;
     if (!h) return fail(WG_E_OOM, "host allocation failed");
     Grid& g = h->g;
@@ -76,8 +77,10 @@ int grid_create(const wg_grid_desc* d, wg_grid** out)
         }
         g.owns = true;
     }
+    g.comp = (d->flags & WG_GRID_COMPENSATED) != 0;
     if (cudaMalloc(&g.norm, sizeof(double) * g.n_chan * g.n_pol) != cudaSuccess ||
-        cudaMalloc(&g.counters, sizeof(unsigned long long) * ST_N) != cudaSuccess) {
+        cudaMalloc(&g.counters, sizeof(unsigned long long) * ST_N) != cudaSuccess ||
+        (g.comp && cudaMalloc(&g.err, bytes) != cudaSuccess)) {
         cudaGetLastError();
         grid_destroy(h);
         return fail(WG_E_OOM, "cannot allocate normaliser");
@@ -99,6 +102,7 @@ int grid_destroy(wg_grid* h)
     if (g.owns) cudaFree(g.data);
     cudaFree(g.norm);
     cudaFree(g.counters);
+    cudaFree(g.err);
     cudaFree(g.scratch);
     cudaFree(g.corr);
     cudaFree(g.icorr);
@@ -113,6 +117,7 @@ int grid_zero(wg_grid* h, void* stream)
     if (!h) return fail(WG_E_INVALID_ARG, "grid_zero: null grid");
     Grid& g = h->g;
     WG_CUDA(cudaMemsetAsync(g.data, 0, sizeof(float2) * (size_t)g.n * g.n * g.n_pol * g.n_chan, S(stream)));
+    if (g.err) WG_CUDA(cudaMemsetAsync(g.err, 0, sizeof(float2) * (size_t)g.n * g.n * g.n_pol * g.n_chan, S(stream)));
     WG_CUDA(cudaMemsetAsync(g.norm, 0, sizeof(double) * g.n_chan * g.n_pol, S(stream)));
     WG_CUDA(cudaMemsetAsync(g.counters, 0, sizeof(unsigned long long) * ST_N, S(stream)));
     return WG_OK;
@@ -138,7 +143,8 @@ int conv_table_build(const wg_table_desc* d, wg_table** out, void* stream)
     if (d->n_k != 0 && (d->n_k < 8 || (d->n_k & 1))) return fail(WG_E_INVALID_ARG, "n_k=%d must be 0 or even >= 8", d->n_k);
     if (!(d->du > 0.0)) return fail(WG_E_INVALID_ARG, "du must be positive");
     if (d->n_wplanes > 1 && !(d->w_max > 0.0)) return fail(WG_E_INVALID_ARG, "w_max must be positive with more than one w-plane");
-    if (d->store_dtype != WG_F32) return fail(WG_E_INVALID_ARG, "store_dtype %d not supported", d->store_dtype);
+    if (d->store_dtype != WG_F32 && d->store_dtype != WG_BF16 && d->store_dtype != WG_F16)
+        return fail(WG_E_INVALID_ARG, "store_dtype %d not supported", d->store_dtype);
     if (d->support_mode == WG_SUPPORT_PRESCRIBED) {
         if (!d->supports) return fail(WG_E_INVALID_ARG, "prescribed supports missing");
         for (int k = 0; k < d->n_wplanes; ++k) {
@@ -153,12 +159,23 @@ int conv_table_build(const wg_table_desc* d, wg_table** out, void* stream)
     wg_table* h = new (std::nothrow) wg_table;
     if (!h) return fail(WG_E_OOM, "host allocation failed");
     int rc = build_table(*d, h->t, S(stream));
+    if (rc == WG_OK && d->store_dtype != WG_F32) {
+        rc = set_table_store(h->t, d->store_dtype);
+        if (rc != WG_OK) free_table(h->t);
+    }
     if (rc != WG_OK) {
         delete h;
         return rc;
     }
     *out = h;
     return WG_OK;
+}
+
+int table_set_store(wg_table* h, int32_t store_dtype)
+{
+    t_err[0] = 0;
+    if (!h) return fail(WG_E_INVALID_ARG, "table_set_store: null table");
+    return set_table_store(h->t, store_dtype);
 }
 
 int conv_table_import(int32_t K, int32_t beta, double w_max, double du, int32_t s0, const int32_t* supports,
@@ -204,6 +221,9 @@ int table_info(const wg_table* h, wg_table_info* info)
     info->zeta = t.zeta;
     info->supports = t.supports_d;
     info->offsets = t.offsets_d;
+    info->store_dtype = t.store;
+    info->reserved = 0;
+    info->data_lp = t.data_lp;
     return WG_OK;
 }
 
@@ -295,7 +315,12 @@ static int check_vis(const Grid& g, const Table& t, const wg_vis_in* in)
         return fail(WG_E_INVALID_ARG, "null input array");
     if (std::fabs(t.du - g.du) > 1e-12 * g.du) return fail(WG_E_SHAPE, "table du %.17g differs from grid du %.17g", t.du, g.du);
     if (t.max_support > g.n) return fail(WG_E_OOB_SUPPORT, "support %d larger than the grid (%d)", t.max_support, g.n);
-    if ((reinterpret_cast<uintptr_t>(in->vis) & 7)) return fail(WG_E_INVALID_ARG, "vis must be 8-byte aligned");
+    if (in->vis_dtype != WG_VIS_COMPLEX64 && in->vis_dtype != WG_VIS_COMPLEX_HALF)
+        return fail(WG_E_INVALID_ARG, "unknown vis_dtype %d", in->vis_dtype);
+    if (in->vis_dtype == WG_VIS_COMPLEX_HALF && in->n_rows > 0 && !in->vis_scale)
+        return fail(WG_E_INVALID_ARG, "vis_scale is required for half-precision visibilities");
+    if ((reinterpret_cast<uintptr_t>(in->vis) & (in->vis_dtype == WG_VIS_COMPLEX64 ? 7 : 3)))
+        return fail(WG_E_INVALID_ARG, "vis is not aligned to its element size");
     return WG_OK;
 }
 

@@ -17,6 +17,9 @@
 // its offsets with the modular wrap and flushes the pixels that changed.  The segment's entries
 // and weighted visibilities are staged in shared memory once per task (cp.async).  R (points per
 // lane) is a template parameter, dispatched per run of records with the same support and channel.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "internal.cuh"
 
 namespace wg {
@@ -77,20 +80,65 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
     return d;
 }
 
-template <int P>
-__device__ __forceinline__ void flush_pixel(float2* __restrict__ gch, int pix, f32x2 (&acc)[P])
+// kernel-table samples: complex float32, bfloat16 or float16, widened to float at use
+__device__ __forceinline__ float2 to_f2(float2 v) { return v; }
+__device__ __forceinline__ float2 to_f2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+__device__ __forceinline__ float2 to_f2(__half2 v) { return __half22float2(v); }
+
+__device__ __forceinline__ float2 load_sample(const float2* p) { return __ldg(p); }
+template <typename TS>
+__device__ __forceinline__ TS load_sample(const TS* p)
+{
+    const unsigned u = __ldg(reinterpret_cast<const unsigned*>(p));
+    TS v;
+    memcpy(&v, &u, sizeof(v));
+    return v;
+}
+
+// exact rounding error of s = fl(a + b) (TwoSum, Knuth)
+__device__ __forceinline__ float two_sum_err(float a, float b, float s)
+{
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    return __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+
+__device__ __forceinline__ float4 add_err4(float4 old, float4 v)
+{
+    return make_float4(two_sum_err(old.x, v.x, __fadd_rn(old.x, v.x)), two_sum_err(old.y, v.y, __fadd_rn(old.y, v.y)),
+                       two_sum_err(old.z, v.z, __fadd_rn(old.z, v.z)), two_sum_err(old.w, v.w, __fadd_rn(old.w, v.w)));
+}
+
+// Adds a lane's accumulators to one pixel.  COMP: the atomic returns the previous value, from
+// which the rounding error of the add is recovered exactly and added to the error grid.
+template <int P, bool COMP>
+__device__ __forceinline__ void flush_pixel(float2* __restrict__ gch, float2* __restrict__ ech, int pix,
+                                            f32x2 (&acc)[P])
 {
     float2* d = gch + (size_t)pix * P;
     float2 a[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) a[p] = unpack2(acc[p]);
     if constexpr (P == 1) {
-        atomicAdd(d, a[0]);
-    } else if constexpr (P == 2) {
-        atomicAdd(reinterpret_cast<float4*>(d), make_float4(a[0].x, a[0].y, a[1].x, a[1].y));
+        if constexpr (COMP) {
+            const float2 o = atomicAdd(d, a[0]);
+            const float2 e = make_float2(two_sum_err(o.x, a[0].x, __fadd_rn(o.x, a[0].x)),
+                                         two_sum_err(o.y, a[0].y, __fadd_rn(o.y, a[0].y)));
+            atomicAdd(ech + pix, e);
+        } else {
+            atomicAdd(d, a[0]);
+        }
     } else {
-        atomicAdd(reinterpret_cast<float4*>(d), make_float4(a[0].x, a[0].y, a[1].x, a[1].y));
-        atomicAdd(reinterpret_cast<float4*>(d + 2), make_float4(a[2].x, a[2].y, a[3].x, a[3].y));
+#pragma unroll
+        for (int h = 0; h < P; h += 2) {
+            const float4 v = make_float4(a[h].x, a[h].y, a[h + 1].x, a[h + 1].y);
+            if constexpr (COMP) {
+                const float4 o = atomicAdd(reinterpret_cast<float4*>(d + h), v);
+                atomicAdd(reinterpret_cast<float4*>(ech + (size_t)pix * P + h), add_err4(o, v));
+            } else {
+                atomicAdd(reinterpret_cast<float4*>(d + h), v);
+            }
+        }
     }
 #pragma unroll
     for (int p = 0; p < P; ++p) acc[p] = 0ull;
@@ -103,10 +151,11 @@ __device__ __forceinline__ int entry_key(const int4& E) { return E.w; }
 // Processes records [j, e1) while their (support, channel) key equals `key` with R <= kRMax
 // points per lane (task block `blk` of the support's footprint); flushes its pixels and returns
 // the first record not processed.  R is warp-uniform: the unrolled point loops stop at R.
-template <int P>
+template <int P, typename TS, bool COMP>
 __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R, int blk, int N, int lane,
-                                           WarpSmem<P>& sm, const float2* __restrict__ table,
-                                           const int* __restrict__ supports, float2* __restrict__ gch)
+                                           WarpSmem<P>& sm, const TS* __restrict__ table,
+                                           const int* __restrict__ supports, float2* __restrict__ gch,
+                                           float2* __restrict__ ech)
 {
     f32x2 acc[kRMax][P];
     int toff[kRMax];
@@ -127,10 +176,10 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
     }
     int fp = -1;             // footprint origin (x0 | y0 << 16) the offsets refer to
     bool pre = false;        // the current buffer holds the current record's samples (prefetched)
-    float2 kva[kRMax], kvb[kRMax];
+    TS kva[kRMax], kvb[kRMax];     // raw samples, widened to float when used
     // One record: load its samples unless prefetched, prefetch the next record's into `nxt` when
     // it keeps the footprint, then accumulate.  Returns false when the run ends at record j.
-    auto step = [&](float2 (&cur_kv)[kRMax], float2 (&nxt)[kRMax]) -> bool {
+    auto step = [&](TS (&cur_kv)[kRMax], TS (&nxt)[kRMax]) -> bool {
         if (j >= e1) return false;
         const int4 E = sm.e[j];
         if (entry_key(E) != key) return false;
@@ -150,29 +199,29 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
                         const int pix = (y0 + dv) * N + x0 + du;
                         const int cur = sm.cur[r][lane];
                         if (pix != cur) {
-                            if (cur >= 0) flush_pixel<P>(gch, cur, acc[r]);
+                            if (cur >= 0) flush_pixel<P, COMP>(gch, ech, cur, acc[r]);
                             sm.cur[r][lane] = pix;
                         }
                     }
                 }
                 fp = E.x;
             }
-            const float2* kz = table + E.z;
+            const TS* kz = table + E.z;
 #pragma unroll
             for (int r = 0; r < kRMax; ++r) {
                 if (r >= R) break;
-                cur_kv[r] = __ldg(kz + toff[r]);   // invalid points read offset 0, never flushed
+                cur_kv[r] = load_sample(kz + toff[r]);   // invalid points read offset 0, never flushed
             }
         }
         pre = false;
         if (j + 1 < e1) {
             const int4 E1 = sm.e[j + 1];
             if (E1.x == fp && entry_key(E1) == key) {
-                const float2* kz = table + E1.z;
+                const TS* kz = table + E1.z;
 #pragma unroll
                 for (int r = 0; r < kRMax; ++r) {
                     if (r >= R) break;
-                    nxt[r] = __ldg(kz + toff[r]);
+                    nxt[r] = load_sample(kz + toff[r]);
                 }
                 pre = true;
             }
@@ -188,7 +237,8 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
 #pragma unroll
         for (int r = 0; r < kRMax; ++r) {
             if (r >= R) break;
-            const f32x2 kxx = pack2(cur_kv[r].x, cur_kv[r].x), kyy = pack2(cur_kv[r].y, cur_kv[r].y);
+            const float2 kv = to_f2(cur_kv[r]);
+            const f32x2 kxx = pack2(kv.x, kv.x), kyy = pack2(kv.y, kv.y);
 #pragma unroll
             for (int p = 0; p < P; ++p) acc[r][p] = fma2(g2[p], kyy, fma2(g1[p], kxx, acc[r][p]));
         }
@@ -202,22 +252,23 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
 #pragma unroll
     for (int r = 0; r < kRMax; ++r) {
         const int cur = sm.cur[r][lane];
-        if (cur >= 0) flush_pixel<P>(gch, cur, acc[r]);
+        if (cur >= 0) flush_pixel<P, COMP>(gch, ech, cur, acc[r]);
     }
     return j;
 }
 
 }  // namespace
 
-template <int P>
+template <int P, typename TS, bool COMP>
 __global__ void __launch_bounds__(kWarps * 32, 4) k_grid(const int4* __restrict__ entries,
                                                          const float2* __restrict__ gamma,
                                                          const int* __restrict__ seg_off,
                                                          const long long* __restrict__ scal,
                                                          const int* __restrict__ supports,
-                                                         const float2* __restrict__ table,
-                                                         float2* __restrict__ grid, int N, int K, int C,
-                                                         int64_t n_samples, unsigned int* __restrict__ counter,
+                                                         const TS* __restrict__ table,
+                                                         float2* __restrict__ grid, float2* __restrict__ errgrid,
+                                                         int N, int K, int C, int64_t n_samples,
+                                                         unsigned int* __restrict__ counter,
                                                          long long* __restrict__ dropped)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -284,6 +335,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_grid(const int4* __restrict_
             }
             const int S = key >> 16, ch = key & 0xFFFF;
             float2* gch = grid + (size_t)ch * chan_stride;
+            float2* ech = COMP ? errgrid + (size_t)ch * chan_stride : nullptr;
             const int s2 = S * S;
             const int nb = (s2 + kSlotsPerBlock - 1) / kSlotsPerBlock;
             const int R = (s2 + 32 * nb - 1) / (32 * nb);
@@ -291,7 +343,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_grid(const int4* __restrict_
                 while (j < n && entry_key(sm.e[j]) == key) ++j;
                 continue;
             }
-            j = run_records<P>(j, n, key, S, R, blk, N, lane, sm, table, supports, gch);
+            j = run_records<P, TS, COMP>(j, n, key, S, R, blk, N, lane, sm, table, supports, gch, ech);
         }
     }
 }
@@ -305,22 +357,60 @@ __global__ void k_accumulate(double* __restrict__ gnorm, const double* __restric
     if (i < ST_N) gcnt[i] += bcnt[i];
 }
 
-template <int P>
-static int grid_impl(Grid& g, const Table& t, const WorkList& wl, cudaStream_t s)
+// grid += err; err = 0 (folds the compensated flushes' rounding errors back)
+__global__ void k_fold(float4* __restrict__ grid, float4* __restrict__ err, int64_t n4)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n4) return;
+    const float4 a = grid[i], e = err[i];
+    grid[i] = make_float4(a.x + e.x, a.y + e.y, a.z + e.z, a.w + e.w);
+    err[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+template <int P, typename TS, bool COMP>
+static int grid_launch(Grid& g, const Table& t, const WorkList& wl, const TS* table, cudaStream_t s)
 {
     static int blocks_per_sm = 0;
     const int smem = (int)(kWarps * sizeof(WarpSmem<P>));
     if (blocks_per_sm == 0) {
-        WG_CUDA(cudaFuncSetAttribute(k_grid<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_grid<P>, kWarps * 32, smem) != cudaSuccess ||
+        WG_CUDA(cudaFuncSetAttribute(k_grid<P, TS, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_grid<P, TS, COMP>, kWarps * 32, smem) !=
+                cudaSuccess ||
             blocks_per_sm < 1)
             blocks_per_sm = 1;
     }
-    WG_CUDA(cudaMemsetAsync(wl.task_counter, 0, sizeof(unsigned int), s));
-    k_grid<P><<<num_sms() * blocks_per_sm, kWarps * 32, smem, s>>>(wl.entries, wl.gamma, wl.seg_off, wl.scal,
-                                                                   t.supports_d, t.data, g.data, g.n, t.K, g.n_chan,
-                                                                   t.n_samples, wl.task_counter, wl.scal + 3);
+    k_grid<P, TS, COMP><<<num_sms() * blocks_per_sm, kWarps * 32, smem, s>>>(
+        wl.entries, wl.gamma, wl.seg_off, wl.scal, t.supports_d, table, g.data, g.err, g.n, t.K, g.n_chan,
+        t.n_samples, wl.task_counter, wl.scal + 3);
     WG_LAUNCHED("k_grid");
+    return WG_OK;
+}
+
+template <int P, bool COMP>
+static int grid_dispatch(Grid& g, const Table& t, const WorkList& wl, cudaStream_t s)
+{
+    switch (t.store) {
+        case WG_BF16:
+            return grid_launch<P, __nv_bfloat162, COMP>(g, t, wl, static_cast<const __nv_bfloat162*>(t.data_lp), s);
+        case WG_F16:
+            return grid_launch<P, __half2, COMP>(g, t, wl, static_cast<const __half2*>(t.data_lp), s);
+        default:
+            return grid_launch<P, float2, COMP>(g, t, wl, t.data, s);
+    }
+}
+
+template <int P>
+static int grid_impl(Grid& g, const Table& t, const WorkList& wl, cudaStream_t s)
+{
+    WG_CUDA(cudaMemsetAsync(wl.task_counter, 0, sizeof(unsigned int), s));
+    const int rc = g.comp ? grid_dispatch<P, true>(g, t, wl, s) : grid_dispatch<P, false>(g, t, wl, s);
+    if (rc != WG_OK) return rc;
+    if (g.comp) {
+        const int64_t n4 = (int64_t)g.n_chan * g.n * g.n * P / 2;
+        k_fold<<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>(reinterpret_cast<float4*>(g.data),
+                                                            reinterpret_cast<float4*>(g.err), n4);
+        WG_LAUNCHED("k_fold");
+    }
     const int n = g.n_chan * g.n_pol;
     const int m = std::max(n, (int)ST_N);
     k_accumulate<<<(m + 255) / 256, 256, 0, s>>>(g.norm, wl.norm_batch, n, g.counters, wl.stats);

@@ -48,6 +48,8 @@ struct Grid {
     double du = 0;
     float2* data = nullptr;
     bool owns = false;
+    bool comp = false;                    // compensated flushes (WG_GRID_COMPENSATED)
+    float2* err = nullptr;                // [n_chan][N][N][P] rounding errors of the flushes
     double* norm = nullptr;               // [n_chan][n_pol]
     unsigned long long* counters = nullptr;  // [8] accumulated statistics
     // grid_correct resources
@@ -66,6 +68,8 @@ struct Table {
     double w_max = 0, du = 0;
     int64_t n_samples = 0;
     float2* data = nullptr;               // C-1, complex float32
+    int store = WG_F32;                   // samples the gridder reads
+    void* data_lp = nullptr;              // C-1 as complex bf16 / f16 (store != WG_F32)
     double* zeta = nullptr;               // C-3 [K beta^2]
     int* supports_d = nullptr;            // C-2 supports [K]
     int* offsets_d = nullptr;             // C-2 offsets [K]
@@ -133,6 +137,7 @@ int build_table(const wg_table_desc& d, Table& t, cudaStream_t s);
 int import_table(int K, int beta, double w_max, double du, int s0, const int* supports,
                  const double* data, const double* zeta, Table& t);
 int free_table(Table& t);
+int set_table_store(Table& t, int store);
 
 // psi_0(c, x) from its even Legendre coefficients a[0..n): sum_m a_m P_2m(x), by the
 // three-term Legendre recurrence.

@@ -18,6 +18,8 @@
 //               kSlotsPerBlock footprint points of its largest support.
 #include <cstdio>
 
+#include <cuda_fp16.h>
+
 #include "internal.cuh"
 
 namespace wg {
@@ -315,8 +317,17 @@ __global__ void k_finalize(int* __restrict__ chan_base, int C, const double* __r
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo, const float2* __restrict__ vis,
+// visibility element -> complex float (half-precision values carry a per-channel scale)
+__device__ __forceinline__ float2 vis_value(const float2* __restrict__ v, int64_t i, float) { return v[i]; }
+__device__ __forceinline__ float2 vis_value(const __half2* __restrict__ v, int64_t i, float scale)
+{
+    const float2 f = __half22float2(v[i]);
+    return make_float2(scale * f.x, scale * f.y);
+}
+
+template <int P, typename VT>
+__global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo, const VT* __restrict__ vis,
+                                                 const float* __restrict__ vis_scale,
                                                  const float* __restrict__ weight, const uint8_t* __restrict__ flag,
                                                  int64_t rows, int rpb, int C, const int* __restrict__ tile_off,
                                                  const int* __restrict__ chan_base, const int* __restrict__ supports,
@@ -335,6 +346,7 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
         if (!((info.w >> kBitG) & 1)) continue;
         const int rank = (info.w >> 16) & 0xFFFF;
         const int dst = chan_base[ch] + tile_off[tile * C + ch] + rank;
+        const float scale = vis_scale ? vis_scale[ch] : 1.0f;
         if (dst < 0 || (int64_t)dst >= cap) {   // cannot happen with a consistent scan
             atomicAdd(reinterpret_cast<unsigned long long*>(&scal[3]), 1ull);
             continue;
@@ -345,7 +357,7 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 const float wf = unweighted ? 1.0f : weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
-                const float2 v = vis[rec * P + p];
+                const float2 v = vis_value(vis, rec * P + p, scale);
                 acc[p] = make_float2(wf * v.x, sg * (wf * v.y));
             }
         }
@@ -358,7 +370,7 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 const float wf = unweighted ? 1.0f : weight[rc2 * P + p] * (1.0f - (float)flag[rc2 * P + p]);
-                const float2 v = vis[rc2 * P + p];
+                const float2 v = vis_value(vis, rc2 * P + p, scale);
                 acc[p].x += wf * v.x;
                 acc[p].y += sg * (wf * v.y);
             }
@@ -426,6 +438,10 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
 {
     const int C = in.n_chan;
     const int64_t rows = in.n_rows;
+    if (in.vis_dtype != WG_VIS_COMPLEX64 && in.vis_dtype != WG_VIS_COMPLEX_HALF)
+        return fail(WG_E_INVALID_ARG, "unknown vis_dtype %d", in.vis_dtype);
+    if (in.vis_dtype == WG_VIS_COMPLEX_HALF && rows > 0 && !in.vis_scale)
+        return fail(WG_E_INVALID_ARG, "vis_scale is required for half-precision visibilities");
     const int rpb = std::max(1, kTileRecords / C);
     const int64_t n_tiles = (rows + rpb - 1) / rpb;
     if ((n_tiles + 1) * C > wl.tile_cap) return fail(WG_E_CAPACITY, "too many tiles for this work list");
@@ -473,10 +489,16 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
     k_finalize<P><<<1, 256, 0, s>>>(wl.chan_base, C, wl.norm_priv, wl.norm_batch, wl.stat_priv, wl.stats, wl.scal);
     WG_LAUNCHED("k_finalize");
     if (rows > 0) {
-        k_compact<P><<<(unsigned)n_tiles, 512, 0, s>>>(wl.rinfo, reinterpret_cast<const float2*>(in.vis), in.weight,
-                                                        in.flag, rows, rpb, C, wl.tile_cnt, wl.chan_base, t.supports_d,
-                                                        wl.entries, wl.gamma, wl.runs, wl.seg_nblk, wl.cap, wl.scal,
-                                                        pp.unweighted);
+        if (in.vis_dtype == WG_VIS_COMPLEX_HALF)
+            k_compact<P, __half2><<<(unsigned)n_tiles, 512, 0, s>>>(
+                wl.rinfo, reinterpret_cast<const __half2*>(in.vis), in.vis_scale, in.weight, in.flag, rows, rpb, C,
+                wl.tile_cnt, wl.chan_base, t.supports_d, wl.entries, wl.gamma, wl.runs, wl.seg_nblk, wl.cap, wl.scal,
+                pp.unweighted);
+        else
+            k_compact<P, float2><<<(unsigned)n_tiles, 512, 0, s>>>(
+                wl.rinfo, reinterpret_cast<const float2*>(in.vis), nullptr, in.weight, in.flag, rows, rpb, C,
+                wl.tile_cnt, wl.chan_base, t.supports_d, wl.entries, wl.gamma, wl.runs, wl.seg_nblk, wl.cap, wl.scal,
+                pp.unweighted);
         WG_LAUNCHED("k_compact");
     }
     k_seg_scan<<<1, 1024, 0, s>>>(wl.seg_nblk, wl.seg_off, wl.scal, wl.stats);

@@ -18,6 +18,9 @@
 #include <cstdio>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "internal.cuh"
 
 namespace wg {
@@ -142,8 +145,41 @@ static int default_nk(int s_max)
     return n;
 }
 
+__global__ void k_table_lp(const float2* __restrict__ src, int64_t n, int store, void* __restrict__ dst)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 v = src[i];
+    if (store == WG_BF16)
+        reinterpret_cast<__nv_bfloat162*>(dst)[i] = __floats2bfloat162_rn(v.x, v.y);
+    else
+        reinterpret_cast<__half2*>(dst)[i] = __floats2half2_rn(v.x, v.y);
+}
+
+int set_table_store(Table& t, int store)
+{
+    if (store != WG_F32 && store != WG_BF16 && store != WG_F16) return fail(WG_E_INVALID_ARG, "unknown store dtype %d", store);
+    cudaFree(t.data_lp);
+    t.data_lp = nullptr;
+    t.store = WG_F32;
+    if (store == WG_F32) return WG_OK;
+    if (cudaMalloc(&t.data_lp, 4 * (size_t)std::max<int64_t>(t.n_samples, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(WG_E_OOM, "cannot allocate the low-precision table");
+    }
+    if (t.n_samples > 0) {
+        k_table_lp<<<(unsigned)((t.n_samples + 255) / 256), 256>>>(t.data, t.n_samples, store, t.data_lp);
+        WG_LAUNCHED("k_table_lp");
+    }
+    WG_CUDA(cudaDeviceSynchronize());
+    t.store = store;
+    return WG_OK;
+}
+
 int free_table(Table& t)
 {
+    cudaFree(t.data_lp);
+    t.data_lp = nullptr;
     cudaFree(t.data);
     cudaFree(t.zeta);
     cudaFree(t.supports_d);

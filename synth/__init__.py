@@ -270,3 +270,15 @@ def make(name: str, device: str = "cpu", flag_frac: float = 0.0, n_times: Option
     flag = _flags(rows, C, P, flag_frac, seed, device)
     return Workload(name, uvw, freq.astype(np.float64), vis, weight, flag, N, du, K, w_max, beta,
                     supports, taper, len(pairs), T_used)
+
+
+def to_half_vis(vis: torch.Tensor, headroom: float = 60000.0):
+    """complex32 visibilities and per-channel float32 scales max|vis| / headroom, so that the
+    scaled values stay inside the float16 range (storage format of the precision variant)."""
+    C = vis.shape[1]
+    amax = vis.abs().amax(dim=(0, 2)) if vis.numel() else torch.zeros(C, device=vis.device)
+    scale = torch.where(amax > 0, amax / headroom, torch.ones_like(amax)).to(torch.float32)
+    import warnings
+    with warnings.catch_warnings():   # complex32 is a storage format here; no arithmetic on it
+        warnings.simplefilter("ignore", UserWarning)
+        return (vis / scale[None, :, None]).to(torch.complex32), scale
