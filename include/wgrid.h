@@ -214,7 +214,8 @@ typedef struct wg_stats {
  *      lam_inv = f_c / 299792458;  sc = lam_inv * (beta / du)
  *      tu = u' sc, tv = v' sc, w = w' lam_inv;  if w' < 0: negate all three, psi = -1
  *      q = ceil(t - 0.5);  x_c = ceil((q - beta/2) / beta) (integer);  frac = q - beta x_c
- *      x = N/2 + x_c;  k = floor((K-1) sqrt(w / w_max) + 0.5)  (k = 0 if K = 1)
+ *      x = N/2 + x_c;  k = floor((K-1) sqrt(w / w_max) + 0.5)  (k = 0 if K = 1), evaluated
+ *      without a square root as the number of plane bounds w_max ((m - 1/2)/(K-1))^2 <= w
  *      footprint origin (x - (S_k-1)/2, y - (S_k-1)/2); kernel pointer
  *      z = offset_k + ((frac_v - lo) beta + (frac_u - lo)) S_k^2, lo = -((beta-1)/2)
  *      griddable: k <= K-1, footprint inside the grid, some polarisation unflagged;
@@ -247,6 +248,38 @@ int worklist_view(const wg_worklist* wl, const int32_t** entries, const void** g
  * "gridding"), FP32 accumulation, and adds the batch's normaliser terms and statistics
  * into the grid.  Persistent kernel over the work list's tasks.  Errors: SHAPE, CUDA. */
 int grid_vis(wg_grid* grid, const wg_table* table, const wg_worklist* wl, void* stream);
+
+/* ---- gridder plan (not in the thesis: GPU work decomposition) ----------------------
+ * grid_vis cuts the work list's gridded entries into segments of seg_len consecutive entries
+ * and each segment's footprint (of its largest support S) into ceil(S^2 / slots) tasks; a
+ * warp runs one task at a time.  vis_compress plans with WG_PLAN_SEG_LEN_DEFAULT and
+ * WG_PLAN_SLOTS_DEFAULT, or with the parameters last given to worklist_plan on this work
+ * list.  The plan changes only the order of the FP32 additions, not what is added. */
+#define WG_PLAN_SEG_LEN_MIN 32
+#define WG_PLAN_SEG_LEN_MAX 256
+#define WG_PLAN_SEG_LEN_DEFAULT 128
+#define WG_PLAN_SLOTS_MIN 64
+#define WG_PLAN_SLOTS_MAX 256
+#define WG_PLAN_SLOTS_DEFAULT 256
+
+/* Re-plans the batch last prepared on `wl` (no repeat of the preparation) and keeps the
+ * parameters for later vis_compress calls.  seg_len and slots: multiples of 32 within the
+ * ranges above.  `table` must be the one given to vis_compress.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, CUDA. */
+int worklist_plan(wg_worklist* wl, const wg_table* table, int32_t seg_len, int32_t slots, void* stream);
+
+/* The work list's current plan parameters. */
+int worklist_get_plan(const wg_worklist* wl, int32_t* seg_len, int32_t* slots);
+
+/* Times grid_vis on the batch prepared on `wl` under every (seg_len, slots) pair of the two
+ * candidate lists (NULL or 0 entries: {64, 128, 256} and {128, 192, 256}), `repeats` timed
+ * launches each after one warm-up launch (CUDA events on `stream`), keeps the fastest plan
+ * in `wl`, writes its mean milliseconds per launch to *best_ms (may be NULL), and then zeroes
+ * the grid (grid_zero: data, normaliser and statistics).  Synchronises `stream`; not to be
+ * captured in a CUDA graph.  Errors: INVALID_ARG, SHAPE, CUDA. */
+int grid_autotune(wg_grid* grid, const wg_table* table, wg_worklist* wl, const int32_t* seg_lens,
+                  int32_t n_seg_lens, const int32_t* slots, int32_t n_slots, int32_t repeats,
+                  float* best_ms, void* stream);
 
 /* A7 (not in the thesis): for every input record, m_p = sum_ij conj(C_k[i][j]) grid_p(y0+i,
  * x0+j), conjugated back where psi = -1; WG_DEGRID_ADJOINT also multiplies by eps (1-f).

@@ -54,10 +54,19 @@ def launch_count() -> int:
 class Grid:
     """Complex64 uv-grids [n_chan][N][N][n_pol] (torch tensor `data`) plus FP64 normalisers."""
 
-    def __init__(self, n: int, du: float, n_pol: int = 1, n_chan: int = 1, device=None, compensated: bool = False):
-        """compensated: flushes recover each atomic add's rounding error (WG_GRID_COMPENSATED)."""
+    def __init__(self, n: int, du: float, n_pol: int = 1, n_chan: int = 1, device=None, compensated: bool = False,
+                 storage: torch.Tensor = None):
+        """compensated: flushes recover each atomic add's rounding error (WG_GRID_COMPENSATED).
+        storage: an existing contiguous complex64 [n_chan][n][n][n_pol] CUDA tensor (e.g. a
+        channel slice of a larger grid) that the grid uses instead of allocating; it is not zeroed."""
         self.n, self.du, self.n_pol, self.n_chan = int(n), float(du), int(n_pol), int(n_chan)
-        self.data = torch.zeros((n_chan, n, n, n_pol), dtype=torch.complex64, device=device or "cuda")
+        if storage is None:
+            self.data = torch.zeros((n_chan, n, n, n_pol), dtype=torch.complex64, device=device or "cuda")
+        else:
+            if (storage.dtype != torch.complex64 or tuple(storage.shape) != (self.n_chan, self.n, self.n, self.n_pol)
+                    or not storage.is_contiguous() or not storage.is_cuda):
+                raise ValueError("storage must be a contiguous complex64 CUDA tensor [n_chan][n][n][n_pol]")
+            self.data = storage
         d = GridDesc(self.n, self.n_pol, self.n_chan, CONST["WG_GRID_COMPENSATED"] if compensated else 0, self.du,
                      self.data.data_ptr())
         h = c_vp()
@@ -216,6 +225,16 @@ class WorkList:
         check(lib.worklist_stats(self._h, ctypes.byref(st), _stream(stream)), "worklist_stats")
         return {k: getattr(st, k) for k, _ in Stats._fields_}
 
+    def plan(self, table: "ConvTable", seg_len: int, slots: int, stream=None):
+        """Re-plans the prepared batch's gridder tasks (segment length, footprint points per task)."""
+        check(lib.worklist_plan(self._h, table.handle, int(seg_len), int(slots), _stream(stream)), "worklist_plan")
+
+    @property
+    def plan_params(self) -> tuple:
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        check(lib.worklist_get_plan(self._h, ctypes.byref(a), ctypes.byref(b)), "worklist_get_plan")
+        return int(a.value), int(b.value)
+
     def view(self, n_records: int, stream=None):
         """(entries int32 [n,4], gamma complex64 [n,P], runs int32 [n,2], rec_class uint8 [n_records])."""
         e, g, r, c = c_vp(), c_vp(), c_vp(), c_vp()
@@ -245,6 +264,22 @@ def vis_compress(grid: Grid, table: ConvTable, batch: VisBatch, worklist: WorkLi
 
 def grid_vis(grid: Grid, table: ConvTable, worklist: WorkList, stream=None):
     check(lib.grid_vis(grid.handle, table.handle, worklist.handle, _stream(stream)), "grid_vis")
+
+
+def grid_autotune(grid: Grid, table: ConvTable, worklist: WorkList, seg_lens=None, slots=None, repeats: int = 3,
+                  stream=None) -> tuple:
+    """Times grid_vis under each candidate plan on the prepared batch, keeps the fastest in the
+    work list and zeroes the grid.  Returns (seg_len, slots, ms per launch)."""
+    def arr(v):
+        if not v:
+            return None, 0
+        return (ctypes.c_int32 * len(v))(*[int(x) for x in v]), len(v)
+    sa, ns = arr(seg_lens)
+    la, nl = arr(slots)
+    ms = ctypes.c_float()
+    check(lib.grid_autotune(grid.handle, table.handle, worklist.handle, sa, ns, la, nl, int(repeats),
+                            ctypes.byref(ms), _stream(stream)), "grid_autotune")
+    return worklist.plan_params + (float(ms.value),)
 
 
 def degrid_vis(grid: Grid, table: ConvTable, batch: VisBatch, worklist: WorkList, mode: int = DEGRID_PREDICT,

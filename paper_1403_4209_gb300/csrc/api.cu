@@ -268,7 +268,7 @@ int worklist_create(int64_t max_records, int32_t C, int32_t P, wg_worklist** out
     const int rpb = std::max(1, kTileRecords / C);
     const int64_t rows_max = (max_records + C - 1) / C;
     w.tile_cap = ((rows_max + rpb - 1) / rpb + 2) * C;
-    w.seg_cap = max_records / kSegLen + 2;
+    w.seg_cap = max_records / kSegLenMin + 2;
     bool ok = true;
     auto al = [&](void** p, size_t bytes) {
         if (ok && cudaMalloc(p, bytes) != cudaSuccess) {
@@ -386,6 +386,102 @@ int grid_vis(wg_grid* gh, const wg_table* th, const wg_worklist* wh, void* strea
     if (w.C != g.n_chan || w.P != g.n_pol) return fail(WG_E_SHAPE, "work list shape differs from the grid's");
     if (w.N != 0 && w.N != g.n) return fail(WG_E_SHAPE, "work list was prepared for N=%d, grid has N=%d", w.N, g.n);
     return launch_grid(g, th->t, w, S(stream));
+}
+
+
+// ---- gridder plan ---------------------------------------------------------------------
+static int check_plan(int seg_len, int slots)
+{
+    if (seg_len < kSegLenMin || seg_len > kSegLenMax || seg_len % 32)
+        return fail(WG_E_INVALID_ARG, "seg_len=%d must be a multiple of 32 in [%d, %d]", seg_len, kSegLenMin,
+                    kSegLenMax);
+    if (slots < kSlotsMin || slots > kSlotsMax || slots % 32)
+        return fail(WG_E_INVALID_ARG, "slots=%d must be a multiple of 32 in [%d, %d]", slots, kSlotsMin, kSlotsMax);
+    return WG_OK;
+}
+
+int worklist_plan(wg_worklist* wh, const wg_table* th, int32_t seg_len, int32_t slots, void* stream)
+{
+    t_err[0] = 0;
+    if (!wh || !th) return fail(WG_E_INVALID_ARG, "worklist_plan: null handle");
+    if (int rc = check_plan(seg_len, slots)) return rc;
+    WorkList& w = wh->w;
+    w.seg_len = seg_len;
+    w.slots = slots;
+    if (w.N == 0) return WG_OK;     // nothing prepared yet: the next vis_compress uses the plan
+    return launch_plan(th->t, w, S(stream));
+}
+
+int worklist_get_plan(const wg_worklist* wh, int32_t* seg_len, int32_t* slots)
+{
+    if (!wh) return fail(WG_E_INVALID_ARG, "worklist_get_plan: null work list");
+    if (seg_len) *seg_len = wh->w.seg_len;
+    if (slots) *slots = wh->w.slots;
+    return WG_OK;
+}
+
+int grid_autotune(wg_grid* gh, const wg_table* th, wg_worklist* wh, const int32_t* seg_lens, int32_t n_seg_lens,
+                  const int32_t* slots, int32_t n_slots, int32_t repeats, float* best_ms, void* stream)
+{
+    t_err[0] = 0;
+    if (!gh || !th || !wh) return fail(WG_E_INVALID_ARG, "grid_autotune: null handle");
+    if (repeats < 1 || repeats > 1000) return fail(WG_E_INVALID_ARG, "repeats=%d must be in [1, 1000]", repeats);
+    static const int32_t def_seg[] = {64, 128, 256}, def_slots[] = {128, 192, 256};
+    if (!seg_lens || n_seg_lens <= 0) {
+        seg_lens = def_seg;
+        n_seg_lens = 3;
+    }
+    if (!slots || n_slots <= 0) {
+        slots = def_slots;
+        n_slots = 3;
+    }
+    for (int i = 0; i < n_seg_lens; ++i)
+        if (int rc = check_plan(seg_lens[i], kSlotsDefault)) return rc;
+    for (int i = 0; i < n_slots; ++i)
+        if (int rc = check_plan(kSegLenDefault, slots[i])) return rc;
+    WorkList& w = wh->w;
+    if (w.N == 0) return fail(WG_E_INVALID_ARG, "grid_autotune: the work list holds no prepared batch");
+    cudaStream_t s = S(stream);
+    cudaEvent_t ev[2];
+    WG_CUDA(cudaEventCreate(&ev[0]));
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return cuda_fail(cudaGetLastError(), "grid_autotune");
+    }
+    float best = -1.f;
+    int best_seg = w.seg_len, best_slots = w.slots, rc = WG_OK;
+    for (int i = 0; i < n_seg_lens && rc == WG_OK; ++i) {
+        for (int k = 0; k < n_slots && rc == WG_OK; ++k) {
+            if ((rc = worklist_plan(wh, th, seg_lens[i], slots[k], stream))) break;
+            if ((rc = grid_vis(gh, th, wh, stream))) break;      // warm-up (occupancy query, caches)
+            if (cudaEventRecord(ev[0], s) != cudaSuccess) {
+                rc = cuda_fail(cudaGetLastError(), "grid_autotune");
+                break;
+            }
+            for (int r = 0; r < repeats && rc == WG_OK; ++r) rc = grid_vis(gh, th, wh, stream);
+            if (rc) break;
+            float ms = 0.f;
+            if (cudaEventRecord(ev[1], s) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) {
+                rc = cuda_fail(cudaGetLastError(), "grid_autotune");
+                break;
+            }
+            ms /= repeats;
+            if (best < 0.f || ms < best) {
+                best = ms;
+                best_seg = seg_lens[i];
+                best_slots = slots[k];
+            }
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc) return rc;
+    if ((rc = worklist_plan(wh, th, best_seg, best_slots, stream))) return rc;
+    if ((rc = grid_zero(gh, stream))) return rc;
+    WG_CUDA(cudaStreamSynchronize(s));
+    if (best_ms) *best_ms = best;
+    return WG_OK;
 }
 
 int degrid_vis(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, const wg_worklist* wh, int32_t mode,

@@ -1,7 +1,7 @@
 // Gridding phase (thesis Sec. 4.3.3 "The gridding phase", eq. "gridding"), GB300 design.
 //
-// Work unit ("task") = one segment of kSegLen consecutive gridded entries x one block of up to
-// kSlotsPerBlock footprint points.  A warp takes tasks from a global counter (persistent
+// Work unit ("task") = one segment of seg_len consecutive gridded entries x one block of up to
+// `slots` footprint points (both chosen by the work list's plan; see grid_autotune).  A warp takes tasks from a global counter (persistent
 // kernel, dynamic load balance).  Each lane owns R <= kRMax fixed residue classes
 // (x mod S, y mod S) of the footprint, the ownership of Romein's algorithm (Sec. 2.5): for
 // every record exactly one grid pixel of each owned class lies inside the S x S footprint, so
@@ -28,12 +28,27 @@ namespace {
 
 constexpr int kWarps = 4;           // warps per block
 
+// One staged record: its entry (w replaced by the key) and weighted visibilities, 16-byte
+// aligned for cp.async (P = 1 pads to 32 bytes).
+template <int P>
+struct StagedRec {
+    int4 e;
+    float2 g[P == 1 ? 2 : P];
+};
+
+// Per-warp shared memory: the residue-class arrays, then seg_len staged records, all at fixed
+// offsets from the warp's base.
 template <int P>
 struct WarpSmem {
-    int4 e[kSegLen];
-    float2 g[kSegLen * P];
-    int puv[kRMax][32];   // each lane's owned residue classes (pu | pv << 16), slow path only
-    int cur[kRMax][32];   // each lane's current pixels, slow path only
+    int (*puv)[32];          // [kRMax][32] each lane's owned residue classes (pu | pv << 16)
+    int (*cur)[32];          // [kRMax][32] each lane's current pixels (slow path only)
+    StagedRec<P>* rec;       // [seg_len]
+    static constexpr size_t kFixed = 2 * kRMax * 32 * sizeof(int);
+    __device__ explicit WarpSmem(unsigned char* base)
+        : puv(reinterpret_cast<int (*)[32]>(base)),
+          cur(reinterpret_cast<int (*)[32]>(base) + kRMax),
+          rec(reinterpret_cast<StagedRec<P>*>(base + kFixed)) {}
+    static constexpr size_t bytes(int seg_len) { return kFixed + (size_t)seg_len * sizeof(StagedRec<P>); }
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p)
@@ -181,7 +196,7 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
     // it keeps the footprint, then accumulate.  Returns false when the run ends at record j.
     auto step = [&](TS (&cur_kv)[kRMax], TS (&nxt)[kRMax]) -> bool {
         if (j >= e1) return false;
-        const int4 E = sm.e[j];
+        const int4 E = sm.rec[j].e;
         if (entry_key(E) != key) return false;
         if (!pre) {
             if (E.x != fp) {     // the footprint moved: new offsets, flush the pixels that change
@@ -215,7 +230,7 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
         }
         pre = false;
         if (j + 1 < e1) {
-            const int4 E1 = sm.e[j + 1];
+            const int4 E1 = sm.rec[j + 1].e;
             if (E1.x == fp && entry_key(E1) == key) {
                 const TS* kz = table + E1.z;
 #pragma unroll
@@ -230,7 +245,7 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
         f32x2 g1[P], g2[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const float2 gm = sm.g[j * P + p];
+            const float2 gm = sm.rec[j].g[p];
             g1[p] = pack2(gm.x, gm.y);
             g2[p] = pack2(-gm.y, gm.x);
         }
@@ -267,13 +282,13 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_grid(const int4* __restrict_
                                                          const int* __restrict__ supports,
                                                          const TS* __restrict__ table,
                                                          float2* __restrict__ grid, float2* __restrict__ errgrid,
-                                                         int N, int K, int C, int64_t n_samples,
-                                                         unsigned int* __restrict__ counter,
+                                                         int N, int K, int C, int64_t n_samples, int seg_len,
+                                                         int slots, unsigned int* __restrict__ counter,
                                                          long long* __restrict__ dropped)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    WarpSmem<P>& sm = reinterpret_cast<WarpSmem<P>*>(smem_raw)[wid];
+    WarpSmem<P> sm(smem_raw + (size_t)wid * WarpSmem<P>::bytes(seg_len));
     const long long n_entries = scal[0], n_tasks = scal[1], n_seg = scal[2];
     const size_t chan_stride = (size_t)N * N * P;
 
@@ -288,18 +303,18 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_grid(const int4* __restrict_
             if (__ldg(&seg_off[mid]) <= (int)t) lo = mid; else hi = mid;
         }
         const int blk = (int)t - __ldg(&seg_off[lo]);
-        const int e0 = lo * kSegLen;
-        const int n = (int)min((long long)kSegLen, n_entries - e0);
+        const int e0 = lo * seg_len;
+        const int n = (int)min((long long)seg_len, n_entries - e0);
 
         // stage the segment's entries and weighted visibilities
         __syncwarp();
         for (int i = lane; i < n; i += 32) {
-            cp_async16(&sm.e[i], entries + e0 + i);
+            cp_async16(&sm.rec[i].e, entries + e0 + i);
             if constexpr (P == 1) {
-                cp_async8(&sm.g[i], gamma + (size_t)(e0 + i));
+                cp_async8(&sm.rec[i].g[0], gamma + (size_t)(e0 + i));
             } else {
 #pragma unroll
-                for (int p = 0; p < P; p += 2) cp_async16(&sm.g[i * P + p], gamma + (size_t)(e0 + i) * P + p);
+                for (int p = 0; p < P; p += 2) cp_async16(&sm.rec[i].g[p], gamma + (size_t)(e0 + i) * P + p);
             }
         }
         cp_commit();
@@ -307,7 +322,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_grid(const int4* __restrict_
         __syncwarp();
         // device-side bounds checks (never taken with a consistent work list)
         for (int i = lane; i < n; i += 32) {
-            const int4 E = sm.e[i];
+            const int4 E = sm.rec[i].e;
             const int k = E.w & 0xFFF, ch = (E.w >> 16) & 0xFFFF;
             bool ok = E.w >= 0 && k < K && ch < C;
             if (ok) {
@@ -318,9 +333,9 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_grid(const int4* __restrict_
                      (int64_t)E.z + (int64_t)S * S <= n_samples;
             }
             if (ok) {
-                sm.e[i].w = (__ldg(&supports[k]) << 16) | ch;
+                sm.rec[i].e.w = (__ldg(&supports[k]) << 16) | ch;
             } else {
-                sm.e[i].w = -1;
+                sm.rec[i].e.w = -1;
                 if (blk == 0) atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
             }
         }
@@ -328,7 +343,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_grid(const int4* __restrict_
 
         int j = 0;
         while (j < n) {
-            const int key = entry_key(sm.e[j]);
+            const int key = entry_key(sm.rec[j].e);
             if (key < 0) {
                 ++j;
                 continue;
@@ -337,10 +352,10 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_grid(const int4* __restrict_
             float2* gch = grid + (size_t)ch * chan_stride;
             float2* ech = COMP ? errgrid + (size_t)ch * chan_stride : nullptr;
             const int s2 = S * S;
-            const int nb = (s2 + kSlotsPerBlock - 1) / kSlotsPerBlock;
+            const int nb = (s2 + slots - 1) / slots;
             const int R = (s2 + 32 * nb - 1) / (32 * nb);
             if (blk >= nb) {     // this block has no points for this support: skip the run
-                while (j < n && entry_key(sm.e[j]) == key) ++j;
+                while (j < n && entry_key(sm.rec[j].e) == key) ++j;
                 continue;
             }
             j = run_records<P, TS, COMP>(j, n, key, S, R, blk, N, lane, sm, table, supports, gch, ech);
@@ -370,18 +385,20 @@ __global__ void k_fold(float4* __restrict__ grid, float4* __restrict__ err, int6
 template <int P, typename TS, bool COMP>
 static int grid_launch(Grid& g, const Table& t, const WorkList& wl, const TS* table, cudaStream_t s)
 {
-    static int blocks_per_sm = 0;
-    const int smem = (int)(kWarps * sizeof(WarpSmem<P>));
-    if (blocks_per_sm == 0) {
-        WG_CUDA(cudaFuncSetAttribute(k_grid<P, TS, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_grid<P, TS, COMP>, kWarps * 32, smem) !=
-                cudaSuccess ||
-            blocks_per_sm < 1)
-            blocks_per_sm = 1;
+    // occupancy per segment length (the shared-memory staging grows with it)
+    static int blocks_per_sm[kSegLenMax / kSegLenMin + 1] = {0};
+    const int smem = (int)(kWarps * WarpSmem<P>::bytes(wl.seg_len));
+    int& bps = blocks_per_sm[wl.seg_len / kSegLenMin];
+    if (bps == 0) {
+        WG_CUDA(cudaFuncSetAttribute(k_grid<P, TS, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kWarps * WarpSmem<P>::bytes(kSegLenMax))));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_grid<P, TS, COMP>, kWarps * 32, smem) != cudaSuccess ||
+            bps < 1)
+            bps = 1;
     }
-    k_grid<P, TS, COMP><<<num_sms() * blocks_per_sm, kWarps * 32, smem, s>>>(
+    k_grid<P, TS, COMP><<<num_sms() * bps, kWarps * 32, smem, s>>>(
         wl.entries, wl.gamma, wl.seg_off, wl.scal, t.supports_d, table, g.data, g.err, g.n, t.K, g.n_chan,
-        t.n_samples, wl.task_counter, wl.scal + 3);
+        t.n_samples, wl.seg_len, wl.slots, wl.task_counter, wl.scal + 3);
     WG_LAUNCHED("k_grid");
     return WG_OK;
 }

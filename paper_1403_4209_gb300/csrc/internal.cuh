@@ -37,8 +37,16 @@ int num_sms();
 constexpr int kMaxSupport = 1023;     // largest odd support
 constexpr int kMaxBeta = 64;
 constexpr int kTileRecords = 2048;    // records per preparation tile (rows x channels)
-constexpr int kSegLen = 128;          // gridded entries per gridder segment
-constexpr int kSlotsPerBlock = 256;   // footprint points per gridder task (32 lanes x 8)
+constexpr int kSegLenMin = 32;        // gridded entries per gridder segment: range and default
+constexpr int kSegLenMax = 256;
+constexpr int kSegLenDefault = 128;
+constexpr int kSlotsMin = 64;         // footprint points per gridder task: range and default
+constexpr int kSlotsMax = 256;        // (32 lanes x kRMax)
+constexpr int kSlotsDefault = 256;
+static_assert(kSegLenMin == WG_PLAN_SEG_LEN_MIN && kSegLenMax == WG_PLAN_SEG_LEN_MAX &&
+                  kSegLenDefault == WG_PLAN_SEG_LEN_DEFAULT && kSlotsMin == WG_PLAN_SLOTS_MIN &&
+                  kSlotsMax == WG_PLAN_SLOTS_MAX && kSlotsDefault == WG_PLAN_SLOTS_DEFAULT,
+              "plan limits differ from the header's");
 constexpr int kRMax = 8;              // points per lane
 constexpr int kNormSlots = 256;       // privatised normaliser accumulators
 
@@ -84,6 +92,8 @@ struct WorkList {
     int C = 0, P = 0;
     int64_t tile_cap = 0;                 // tiles x C counters
     int64_t seg_cap = 0;
+    int seg_len = kSegLenDefault;         // gridder plan: entries per segment
+    int slots = kSlotsDefault;            // gridder plan: footprint points per task
     // per record
     int4* rinfo = nullptr;
     uint8_t* rclass = nullptr;
@@ -130,6 +140,7 @@ struct PlaceParams {
 int launch_prep(const Table& t, const Grid& g, const wg_vis_in& in, int flags, WorkList& wl,
                 cudaStream_t s);
 int launch_grid(Grid& g, const Table& t, const WorkList& wl, cudaStream_t s);
+int launch_plan(const Table& t, WorkList& wl, cudaStream_t s);
 int launch_degrid(const Grid& g, const Table& t, const wg_vis_in& in, const WorkList& wl, int mode,
                   float2* out, cudaStream_t s);
 int launch_correct(Grid& g, const Table& t, int mode, float* image, cudaStream_t s);

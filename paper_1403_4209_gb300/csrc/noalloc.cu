@@ -103,7 +103,7 @@ extern "C" int grid_vis_noalloc(const wg_grid_view* view, const wg_table* th, co
     const int rpb = std::max(1, kTileRecords / C);
     const int64_t rows_max = (cap + C - 1) / C;
     w.tile_cap = ((rows_max + rpb - 1) / rpb + 2) * C;
-    w.seg_cap = cap / kSegLen + 2;
+    w.seg_cap = cap / kSegLenMin + 2;
     Carver cv{static_cast<unsigned char*>(base)};
     w.rinfo = cv.take<int4>(cap);
     w.rclass = cv.take<uint8_t>(cap);

@@ -13,9 +13,10 @@
 //   k_compact   (Compress Index Generate + Compress and Weigh Visibilities, Algorithm
 //               "compressindex", eqs. "compress1"/"conjugatetake"): each gridded record
 //               walks its run of compressed successors and sums eps (1-f) psi-conj(vis).
-//   k_seg_scan  (Plan Create / Plan Analyse, Algorithm "plan"): gridded entries are cut into
-//               segments of kSegLen entries; each segment needs one gridder task per block of
-//               kSlotsPerBlock footprint points of its largest support.
+//   k_segments + k_seg_scan (Plan Create / Plan Analyse, Algorithm "plan"): gridded entries
+//               are cut into segments of seg_len entries; each segment needs one gridder task
+//               per block of `slots` footprint points of its largest support.  The plan can be
+//               redone with other parameters (launch_plan) without repeating the preparation.
 #include <cstdio>
 
 #include <cuda_fp16.h>
@@ -88,10 +89,10 @@ __device__ __forceinline__ Placed place(const double* __restrict__ uvw, int64_t 
     return o;
 }
 
-__device__ __forceinline__ int nblk_of(int S)
+__device__ __forceinline__ int nblk_of(int S, int slots)
 {
     const int s2 = S * S;
-    return (s2 + kSlotsPerBlock - 1) / kSlotsPerBlock;
+    return (s2 + slots - 1) / slots;
 }
 
 // exclusive block scan of a[0..n) in place; a[n] = total.  Needs blockDim multiple of 32.
@@ -303,7 +304,6 @@ __global__ void k_finalize(int* __restrict__ chan_base, int C, const double* __r
         }
         chan_base[C] = (int)run;
         scal[0] = run;
-        scal[2] = (run + kSegLen - 1) / kSegLen;
     }
     for (int i = threadIdx.x; i < C * P; i += blockDim.x) {
         double s = 0.0;
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
                                                  int64_t rows, int rpb, int C, const int* __restrict__ tile_off,
                                                  const int* __restrict__ chan_base, const int* __restrict__ supports,
                                                  int4* __restrict__ entries, float2* __restrict__ gamma,
-                                                 int2* __restrict__ runs, int* __restrict__ seg_nblk, int64_t cap,
+                                                 int2* __restrict__ runs, int64_t cap,
                                                  long long* __restrict__ scal, int unweighted)
 {
     const int64_t tile = blockIdx.x;
@@ -381,7 +381,20 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
 #pragma unroll
         for (int p = 0; p < P; ++p) gamma[(int64_t)dst * P + p] = acc[p];
         runs[dst] = make_int2((int)row, (int)last);
-        atomicMax(&seg_nblk[dst / kSegLen], nblk_of(__ldg(&supports[k])));
+    }
+}
+
+// per segment, the number of task blocks of its largest support; sets the segment count
+__global__ void k_segments(const int4* __restrict__ entries, long long* __restrict__ scal,
+                           const int* __restrict__ supports, int K, int seg_len, int slots,
+                           int* __restrict__ seg_nblk)
+{
+    const long long n = scal[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) scal[2] = (n + seg_len - 1) / seg_len;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int k = entries[e].w & 0xFFF;
+        const int nb = (k < K) ? nblk_of(__ldg(&supports[k]), slots) : 1;
+        atomicMax(&seg_nblk[e / seg_len], nb);
     }
 }
 
@@ -471,7 +484,6 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
 
     WG_CUDA(cudaMemsetAsync(wl.norm_priv, 0, sizeof(double) * kNormSlots * C * P, s));
     WG_CUDA(cudaMemsetAsync(wl.stat_priv, 0, sizeof(unsigned long long) * kNormSlots * ST_N, s));
-    WG_CUDA(cudaMemsetAsync(wl.seg_nblk, 0, sizeof(int) * wl.seg_cap, s));
     WG_CUDA(cudaMemsetAsync(wl.stats, 0, sizeof(unsigned long long) * ST_N, s));
     WG_CUDA(cudaMemsetAsync(wl.scal, 0, sizeof(long long) * 4, s));
 
@@ -492,15 +504,25 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
         if (in.vis_dtype == WG_VIS_COMPLEX_HALF)
             k_compact<P, __half2><<<(unsigned)n_tiles, 512, 0, s>>>(
                 wl.rinfo, reinterpret_cast<const __half2*>(in.vis), in.vis_scale, in.weight, in.flag, rows, rpb, C,
-                wl.tile_cnt, wl.chan_base, t.supports_d, wl.entries, wl.gamma, wl.runs, wl.seg_nblk, wl.cap, wl.scal,
+                wl.tile_cnt, wl.chan_base, t.supports_d, wl.entries, wl.gamma, wl.runs, wl.cap, wl.scal,
                 pp.unweighted);
         else
             k_compact<P, float2><<<(unsigned)n_tiles, 512, 0, s>>>(
                 wl.rinfo, reinterpret_cast<const float2*>(in.vis), nullptr, in.weight, in.flag, rows, rpb, C,
-                wl.tile_cnt, wl.chan_base, t.supports_d, wl.entries, wl.gamma, wl.runs, wl.seg_nblk, wl.cap, wl.scal,
+                wl.tile_cnt, wl.chan_base, t.supports_d, wl.entries, wl.gamma, wl.runs, wl.cap, wl.scal,
                 pp.unweighted);
         WG_LAUNCHED("k_compact");
     }
+    return launch_plan(t, wl, s);
+}
+
+int launch_plan(const Table& t, WorkList& wl, cudaStream_t s)
+{
+    const int64_t n_seg_max = (wl.cap + wl.seg_len - 1) / wl.seg_len + 1;
+    WG_CUDA(cudaMemsetAsync(wl.seg_nblk, 0, sizeof(int) * std::min<int64_t>(n_seg_max, wl.seg_cap), s));
+    k_segments<<<num_sms() * 4, 256, 0, s>>>(wl.entries, wl.scal, t.supports_d, t.K, wl.seg_len, wl.slots,
+                                              wl.seg_nblk);
+    WG_LAUNCHED("k_segments");
     k_seg_scan<<<1, 1024, 0, s>>>(wl.seg_nblk, wl.seg_off, wl.scal, wl.stats);
     WG_LAUNCHED("k_seg_scan");
     return WG_OK;

@@ -168,7 +168,19 @@ class Workload:
 
     @property
     def n_pol(self):
-        return self.vis.shape[2]
+        v = self.vis[0] if isinstance(self.vis, list) else self.vis
+        return v.shape[2]
+
+    @property
+    def chan_groups(self):
+        """[(c0, c1)] channel ranges of the per-group tensors (one range if not grouped)."""
+        if not isinstance(self.vis, list):
+            return [(0, self.n_chan)]
+        out, c0 = [], 0
+        for v in self.vis:
+            out.append((c0, c0 + v.shape[1]))
+            c0 += v.shape[1]
+        return out
 
 
 def support_schedule(s_min: int, s_max: int, k_planes: int) -> list:
@@ -205,7 +217,8 @@ def _flags(rows, C, P, frac, seed, device):
 
 
 def make(name: str, device: str = "cpu", flag_frac: float = 0.0, n_times: Optional[int] = None,
-         n_chan: Optional[int] = None, n_baselines: Optional[int] = None) -> Workload:
+         n_chan: Optional[int] = None, n_baselines: Optional[int] = None,
+         chan_group: Optional[int] = None) -> Workload:
     """Build one of the named workloads.
 
     name: "w0_small"   : plain w=0 gridding, 32 stations in a 2 km disk, 496 baselines x 256
@@ -216,7 +229,10 @@ def make(name: str, device: str = "cpu", flag_frac: float = 0.0, n_times: Option
           "degrid_1k"  : 64 stations, 600 steps, 4 channels 120-180 MHz, 4 pols, N=1024, K=16.
           "batch_8k"   : 256 stations log-radial to 10 km, 1800 steps, 64 channels
                          50-350 MHz, 1 pol, N=8192, K=64, supports 9..129.
-    n_times / n_chan / n_baselines shrink a workload to a seeded slice of the same geometry."""
+    n_times / n_chan / n_baselines shrink a workload to a seeded slice of the same geometry.
+    chan_group: vis, weight and flag become lists of [rows, chan_group, P] tensors, one per
+    group of consecutive channels, each drawn with its own seed (seed + 7919 * group index);
+    the (all-ones) weight tensor is shared by the groups."""
     seeds = {"w0_small": 1000, "wproj_2k": 1001, "degrid_1k": 1002, "batch_8k": 1004}
     seed = seeds[name]
     rng = np.random.default_rng(seed)
@@ -265,9 +281,20 @@ def make(name: str, device: str = "cpu", flag_frac: float = 0.0, n_times: Option
     if n_chan is not None:
         freq = freq[:n_chan]
     rows, C = uvw.shape[0], freq.shape[0]
-    vis = visibilities(uvw, freq, sky, P, noise, seed, device=device)
-    weight = torch.ones((rows, C, P), dtype=torch.float32, device=device)
-    flag = _flags(rows, C, P, flag_frac, seed, device)
+    if chan_group is None:
+        vis = visibilities(uvw, freq, sky, P, noise, seed, device=device)
+        weight = torch.ones((rows, C, P), dtype=torch.float32, device=device)
+        flag = _flags(rows, C, P, flag_frac, seed, device)
+    else:
+        if C % chan_group:
+            raise ValueError("chan_group=%d must divide the %d channels" % (chan_group, C))
+        ones = torch.ones((rows, chan_group, P), dtype=torch.float32, device=device)
+        vis, weight, flag = [], [], []
+        for gi, c0 in enumerate(range(0, C, chan_group)):
+            sg = seed + 7919 * gi
+            vis.append(visibilities(uvw, freq[c0:c0 + chan_group], sky, P, noise, sg, device=device))
+            weight.append(ones)
+            flag.append(_flags(rows, chan_group, P, flag_frac, sg, device))
     return Workload(name, uvw, freq.astype(np.float64), vis, weight, flag, N, du, K, w_max, beta,
                     supports, taper, len(pairs), T_used)
 

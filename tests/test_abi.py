@@ -72,3 +72,13 @@ def test_worklist_and_null_handles():
 def test_errors_raise_in_python():
     with pytest.raises(wg.WgError, match="WG_E_INVALID_ARG"):
         _lib.check(wg.lib.worklist_create(0, 1, 1, ctypes.byref(ctypes.c_void_p())), "worklist_create")
+
+
+def test_plan_limits_and_null_handles():
+    assert C["WG_PLAN_SEG_LEN_MIN"] <= C["WG_PLAN_SEG_LEN_DEFAULT"] <= C["WG_PLAN_SEG_LEN_MAX"]
+    assert C["WG_PLAN_SLOTS_MIN"] <= C["WG_PLAN_SLOTS_DEFAULT"] <= C["WG_PLAN_SLOTS_MAX"]
+    assert all(C[k] % 32 == 0 for k in C if k.startswith("WG_PLAN_"))
+    assert wg.lib.worklist_plan(None, None, 128, 256, None) == C["WG_E_INVALID_ARG"]
+    assert "null" in _err()
+    assert wg.lib.worklist_get_plan(None, None, None) == C["WG_E_INVALID_ARG"]
+    assert wg.lib.grid_autotune(None, None, None, None, 0, None, 0, 3, None, None) == C["WG_E_INVALID_ARG"]
