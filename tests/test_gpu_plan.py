@@ -47,7 +47,7 @@ def test_plan_grids_the_same_sums(case, seg_len, slots):
     assert rel_l2(got, ref["grid"]) < 1e-5 and max_rel(got, ref["grid"]) < 1e-4
     assert st["dropped"] == 0
     assert st["tasks"] == _tasks(gpu["entries"], t.supports, seg_len, slots)
-    np.testing.assert_allclose(g.normaliser().cpu().numpy(), ref["norm"], rtol=1e-6)
+    assert max_rel(g.normaliser().cpu().numpy(), ref["norm"]) < 1e-5    # FP32 per-tile partials
 
 
 def test_plan_rejects_bad_parameters(case):
