@@ -252,34 +252,45 @@ int grid_vis(wg_grid* grid, const wg_table* table, const wg_worklist* wl, void* 
 /* ---- gridder plan (not in the thesis: GPU work decomposition) ----------------------
  * grid_vis cuts the work list's gridded entries into segments of seg_len consecutive entries
  * and each segment's footprint (of its largest support S) into ceil(S^2 / slots) tasks; a
- * warp runs one task at a time.  vis_compress plans with WG_PLAN_SEG_LEN_DEFAULT and
- * WG_PLAN_SLOTS_DEFAULT, or with the parameters last given to worklist_plan on this work
- * list.  The plan changes only the order of the FP32 additions, not what is added. */
+ * warp runs one task at a time with R points per lane.  By default R = ceil(S^2 / (32 x
+ * tasks)) per support; with WG_PLAN_FIXED_R, R = slots / 32 for every support (no per-point
+ * checks; the last task of a small support then has idle points).  FIXED_R takes effect for
+ * slots 128 and 256 on FP32 tables without compensation; elsewhere the per-support R runs.
+ * vis_compress plans with the work list's current plan (initially WG_PLAN_SEG_LEN_DEFAULT,
+ * WG_PLAN_SLOTS_DEFAULT, no flags).  The plan changes only the order of the FP32 additions,
+ * not what is added. */
 #define WG_PLAN_SEG_LEN_MIN 32
 #define WG_PLAN_SEG_LEN_MAX 256
 #define WG_PLAN_SEG_LEN_DEFAULT 128
 #define WG_PLAN_SLOTS_MIN 64
 #define WG_PLAN_SLOTS_MAX 256
 #define WG_PLAN_SLOTS_DEFAULT 256
+#define WG_PLAN_FIXED_R 1
 
-/* Re-plans the batch last prepared on `wl` (no repeat of the preparation) and keeps the
- * parameters for later vis_compress calls.  seg_len and slots: multiples of 32 within the
- * ranges above.  `table` must be the one given to vis_compress.  Asynchronous on `stream`.
+typedef struct wg_plan {
+    int32_t seg_len;        /* gridded entries per segment: a multiple of 32 in [MIN, MAX] */
+    int32_t slots;          /* footprint points per task: a multiple of 32 in [MIN, MAX]   */
+    int32_t flags;          /* 0 or WG_PLAN_FIXED_R                                          */
+    int32_t reserved;       /* 0                                                              */
+} wg_plan;
+
+/* Sets the work list's plan and re-plans the batch last prepared on it (no repeat of the
+ * preparation).  `table` must be the one given to vis_compress.  Asynchronous on `stream`.
  * Errors: INVALID_ARG, CUDA. */
-int worklist_plan(wg_worklist* wl, const wg_table* table, int32_t seg_len, int32_t slots, void* stream);
+int worklist_plan(wg_worklist* wl, const wg_table* table, const wg_plan* plan, void* stream);
 
-/* The work list's current plan parameters. */
-int worklist_get_plan(const wg_worklist* wl, int32_t* seg_len, int32_t* slots);
+/* The work list's current plan. */
+int worklist_get_plan(const wg_worklist* wl, wg_plan* plan);
 
-/* Times grid_vis on the batch prepared on `wl` under every (seg_len, slots) pair of the two
- * candidate lists (NULL or 0 entries: {64, 128, 256} and {128, 192, 256}), `repeats` timed
- * launches each after one warm-up launch (CUDA events on `stream`), keeps the fastest plan
- * in `wl`, writes its mean milliseconds per launch to *best_ms (may be NULL), and then zeroes
- * the grid (grid_zero: data, normaliser and statistics).  Synchronises `stream`; not to be
- * captured in a CUDA graph.  Errors: INVALID_ARG, SHAPE, CUDA. */
-int grid_autotune(wg_grid* grid, const wg_table* table, wg_worklist* wl, const int32_t* seg_lens,
-                  int32_t n_seg_lens, const int32_t* slots, int32_t n_slots, int32_t repeats,
-                  float* best_ms, void* stream);
+/* Times grid_vis on the batch prepared on `wl` under each of the n_candidates plans (NULL or
+ * 0: seg_len {64, 128, 256} x slots {128, 256} x flags {0, WG_PLAN_FIXED_R}), `repeats`
+ * timed launches each after one warm-up launch (CUDA events on `stream`), keeps the fastest
+ * plan in `wl` and copies it to *best (may be NULL), writes its mean milliseconds per launch
+ * to *best_ms (may be NULL), and then zeroes the grid (grid_zero: data, normaliser and
+ * statistics).  Synchronises `stream`; not to be captured in a CUDA graph.
+ * Errors: INVALID_ARG, SHAPE, CUDA. */
+int grid_autotune(wg_grid* grid, const wg_table* table, wg_worklist* wl, const wg_plan* candidates,
+                  int32_t n_candidates, int32_t repeats, wg_plan* best, float* best_ms, void* stream);
 
 /* A7 (not in the thesis): for every input record, m_p = sum_ij conj(C_k[i][j]) grid_p(y0+i,
  * x0+j), conjugated back where psi = -1; WG_DEGRID_ADJOINT also multiplies by eps (1-f).

@@ -44,6 +44,10 @@ class Stats(ctypes.Structure):
                                      "updates_saved", "tasks", "dropped")]
 
 
+class Plan(ctypes.Structure):
+    _fields_ = [("seg_len", c_i32), ("slots", c_i32), ("flags", c_i32), ("reserved", c_i32)]
+
+
 def _constants():
     out = {}
     for m in re.finditer(r"#define\s+(WG_\w+)\s+\(?(-?\d+)\)?", open(HEADER).read()):
@@ -89,9 +93,9 @@ def _load():
         "worklist_stats": (c_i32, [c_vp, P(Stats), c_vp]),
         "worklist_view": (c_i32, [c_vp, P(c_vp), P(c_vp), P(c_vp), P(c_vp), P(c_i64), c_vp]),
         "grid_vis": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
-        "worklist_plan": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_vp]),
-        "worklist_get_plan": (c_i32, [c_vp, P(c_i32), P(c_i32)]),
-        "grid_autotune": (c_i32, [c_vp, c_vp, c_vp, P(c_i32), c_i32, P(c_i32), c_i32, c_i32, P(ctypes.c_float), c_vp]),
+        "worklist_plan": (c_i32, [c_vp, c_vp, P(Plan), c_vp]),
+        "worklist_get_plan": (c_i32, [c_vp, P(Plan)]),
+        "grid_autotune": (c_i32, [c_vp, c_vp, c_vp, P(Plan), c_i32, c_i32, P(Plan), P(ctypes.c_float), c_vp]),
         "degrid_vis": (c_i32, [c_vp, c_vp, P(VisIn), c_vp, c_i32, c_vp, c_vp]),
         "grid_correct": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
     }

@@ -10,7 +10,7 @@ import ctypes
 import numpy as np
 import torch
 
-from ._lib import CONST, GridDesc, Stats, TableDesc, TableInfo, VisIn, check, lib
+from ._lib import Plan, CONST, GridDesc, Stats, TableDesc, TableInfo, VisIn, check, lib
 
 c_vp = ctypes.c_void_p
 
@@ -225,15 +225,18 @@ class WorkList:
         check(lib.worklist_stats(self._h, ctypes.byref(st), _stream(stream)), "worklist_stats")
         return {k: getattr(st, k) for k, _ in Stats._fields_}
 
-    def plan(self, table: "ConvTable", seg_len: int, slots: int, stream=None):
-        """Re-plans the prepared batch's gridder tasks (segment length, footprint points per task)."""
-        check(lib.worklist_plan(self._h, table.handle, int(seg_len), int(slots), _stream(stream)), "worklist_plan")
+    def plan(self, table: "ConvTable", seg_len: int, slots: int, fixed_r: bool = False, stream=None):
+        """Re-plans the prepared batch's gridder tasks: segment length, footprint points per task,
+        and whether every support runs with R = slots / 32 points per lane (WG_PLAN_FIXED_R)."""
+        pl = Plan(int(seg_len), int(slots), CONST["WG_PLAN_FIXED_R"] if fixed_r else 0, 0)
+        check(lib.worklist_plan(self._h, table.handle, ctypes.byref(pl), _stream(stream)), "worklist_plan")
 
     @property
     def plan_params(self) -> tuple:
-        a, b = ctypes.c_int32(), ctypes.c_int32()
-        check(lib.worklist_get_plan(self._h, ctypes.byref(a), ctypes.byref(b)), "worklist_get_plan")
-        return int(a.value), int(b.value)
+        """(seg_len, slots, fixed_r) of the current plan."""
+        pl = Plan()
+        check(lib.worklist_get_plan(self._h, ctypes.byref(pl)), "worklist_get_plan")
+        return int(pl.seg_len), int(pl.slots), bool(pl.flags & CONST["WG_PLAN_FIXED_R"])
 
     def view(self, n_records: int, stream=None):
         """(entries int32 [n,4], gamma complex64 [n,P], runs int32 [n,2], rec_class uint8 [n_records])."""
@@ -266,20 +269,19 @@ def grid_vis(grid: Grid, table: ConvTable, worklist: WorkList, stream=None):
     check(lib.grid_vis(grid.handle, table.handle, worklist.handle, _stream(stream)), "grid_vis")
 
 
-def grid_autotune(grid: Grid, table: ConvTable, worklist: WorkList, seg_lens=None, slots=None, repeats: int = 3,
+def grid_autotune(grid: Grid, table: ConvTable, worklist: WorkList, candidates=None, repeats: int = 3,
                   stream=None) -> tuple:
-    """Times grid_vis under each candidate plan on the prepared batch, keeps the fastest in the
-    work list and zeroes the grid.  Returns (seg_len, slots, ms per launch)."""
-    def arr(v):
-        if not v:
-            return None, 0
-        return (ctypes.c_int32 * len(v))(*[int(x) for x in v]), len(v)
-    sa, ns = arr(seg_lens)
-    la, nl = arr(slots)
-    ms = ctypes.c_float()
-    check(lib.grid_autotune(grid.handle, table.handle, worklist.handle, sa, ns, la, nl, int(repeats),
+    """Times grid_vis under each candidate plan (seg_len, slots, fixed_r) on the prepared batch
+    (None: the library's default list), keeps the fastest in the work list and zeroes the grid.
+    Returns (seg_len, slots, fixed_r, ms per launch)."""
+    arr, n = None, 0
+    if candidates:
+        n = len(candidates)
+        arr = (Plan * n)(*[Plan(int(a), int(b), CONST["WG_PLAN_FIXED_R"] if c else 0, 0) for a, b, c in candidates])
+    best, ms = Plan(), ctypes.c_float()
+    check(lib.grid_autotune(grid.handle, table.handle, worklist.handle, arr, n, int(repeats), ctypes.byref(best),
                             ctypes.byref(ms), _stream(stream)), "grid_autotune")
-    return worklist.plan_params + (float(ms.value),)
+    return int(best.seg_len), int(best.slots), bool(best.flags & CONST["WG_PLAN_FIXED_R"]), float(ms.value)
 
 
 def degrid_vis(grid: Grid, table: ConvTable, batch: VisBatch, worklist: WorkList, mode: int = DEGRID_PREDICT,

@@ -390,55 +390,56 @@ int grid_vis(wg_grid* gh, const wg_table* th, const wg_worklist* wh, void* strea
 
 
 // ---- gridder plan ---------------------------------------------------------------------
-static int check_plan(int seg_len, int slots)
+static int check_plan(const wg_plan& p)
 {
-    if (seg_len < kSegLenMin || seg_len > kSegLenMax || seg_len % 32)
-        return fail(WG_E_INVALID_ARG, "seg_len=%d must be a multiple of 32 in [%d, %d]", seg_len, kSegLenMin,
+    if (p.seg_len < kSegLenMin || p.seg_len > kSegLenMax || p.seg_len % 32)
+        return fail(WG_E_INVALID_ARG, "seg_len=%d must be a multiple of 32 in [%d, %d]", p.seg_len, kSegLenMin,
                     kSegLenMax);
-    if (slots < kSlotsMin || slots > kSlotsMax || slots % 32)
-        return fail(WG_E_INVALID_ARG, "slots=%d must be a multiple of 32 in [%d, %d]", slots, kSlotsMin, kSlotsMax);
+    if (p.slots < kSlotsMin || p.slots > kSlotsMax || p.slots % 32)
+        return fail(WG_E_INVALID_ARG, "slots=%d must be a multiple of 32 in [%d, %d]", p.slots, kSlotsMin, kSlotsMax);
+    if (p.flags & ~WG_PLAN_FIXED_R) return fail(WG_E_INVALID_ARG, "unknown plan flags %d", p.flags);
     return WG_OK;
 }
 
-int worklist_plan(wg_worklist* wh, const wg_table* th, int32_t seg_len, int32_t slots, void* stream)
+int worklist_plan(wg_worklist* wh, const wg_table* th, const wg_plan* plan, void* stream)
 {
     t_err[0] = 0;
-    if (!wh || !th) return fail(WG_E_INVALID_ARG, "worklist_plan: null handle");
-    if (int rc = check_plan(seg_len, slots)) return rc;
+    if (!wh || !th || !plan) return fail(WG_E_INVALID_ARG, "worklist_plan: null argument");
+    if (int rc = check_plan(*plan)) return rc;
     WorkList& w = wh->w;
-    w.seg_len = seg_len;
-    w.slots = slots;
+    w.seg_len = plan->seg_len;
+    w.slots = plan->slots;
+    w.fixed_r = (plan->flags & WG_PLAN_FIXED_R) != 0;
     if (w.N == 0) return WG_OK;     // nothing prepared yet: the next vis_compress uses the plan
     return launch_plan(th->t, w, S(stream));
 }
 
-int worklist_get_plan(const wg_worklist* wh, int32_t* seg_len, int32_t* slots)
+int worklist_get_plan(const wg_worklist* wh, wg_plan* plan)
 {
-    if (!wh) return fail(WG_E_INVALID_ARG, "worklist_get_plan: null work list");
-    if (seg_len) *seg_len = wh->w.seg_len;
-    if (slots) *slots = wh->w.slots;
+    if (!wh || !plan) return fail(WG_E_INVALID_ARG, "worklist_get_plan: null argument");
+    plan->seg_len = wh->w.seg_len;
+    plan->slots = wh->w.slots;
+    plan->flags = wh->w.fixed_r ? WG_PLAN_FIXED_R : 0;
+    plan->reserved = 0;
     return WG_OK;
 }
 
-int grid_autotune(wg_grid* gh, const wg_table* th, wg_worklist* wh, const int32_t* seg_lens, int32_t n_seg_lens,
-                  const int32_t* slots, int32_t n_slots, int32_t repeats, float* best_ms, void* stream)
+int grid_autotune(wg_grid* gh, const wg_table* th, wg_worklist* wh, const wg_plan* cands, int32_t n_cands,
+                  int32_t repeats, wg_plan* best_out, float* best_ms, void* stream)
 {
     t_err[0] = 0;
     if (!gh || !th || !wh) return fail(WG_E_INVALID_ARG, "grid_autotune: null handle");
     if (repeats < 1 || repeats > 1000) return fail(WG_E_INVALID_ARG, "repeats=%d must be in [1, 1000]", repeats);
-    static const int32_t def_seg[] = {64, 128, 256}, def_slots[] = {128, 192, 256};
-    if (!seg_lens || n_seg_lens <= 0) {
-        seg_lens = def_seg;
-        n_seg_lens = 3;
+    std::vector<wg_plan> list;
+    if (cands && n_cands > 0) {
+        list.assign(cands, cands + n_cands);
+    } else {
+        for (int seg : {64, 128, 256})
+            for (int slots : {128, 256})
+                for (int flags : {0, WG_PLAN_FIXED_R}) list.push_back(wg_plan{seg, slots, flags, 0});
     }
-    if (!slots || n_slots <= 0) {
-        slots = def_slots;
-        n_slots = 3;
-    }
-    for (int i = 0; i < n_seg_lens; ++i)
-        if (int rc = check_plan(seg_lens[i], kSlotsDefault)) return rc;
-    for (int i = 0; i < n_slots; ++i)
-        if (int rc = check_plan(kSegLenDefault, slots[i])) return rc;
+    for (const wg_plan& p : list)
+        if (int rc = check_plan(p)) return rc;
     WorkList& w = wh->w;
     if (w.N == 0) return fail(WG_E_INVALID_ARG, "grid_autotune: the work list holds no prepared batch");
     cudaStream_t s = S(stream);
@@ -449,37 +450,36 @@ int grid_autotune(wg_grid* gh, const wg_table* th, wg_worklist* wh, const int32_
         return cuda_fail(cudaGetLastError(), "grid_autotune");
     }
     float best = -1.f;
-    int best_seg = w.seg_len, best_slots = w.slots, rc = WG_OK;
-    for (int i = 0; i < n_seg_lens && rc == WG_OK; ++i) {
-        for (int k = 0; k < n_slots && rc == WG_OK; ++k) {
-            if ((rc = worklist_plan(wh, th, seg_lens[i], slots[k], stream))) break;
-            if ((rc = grid_vis(gh, th, wh, stream))) break;      // warm-up (occupancy query, caches)
-            if (cudaEventRecord(ev[0], s) != cudaSuccess) {
-                rc = cuda_fail(cudaGetLastError(), "grid_autotune");
-                break;
-            }
-            for (int r = 0; r < repeats && rc == WG_OK; ++r) rc = grid_vis(gh, th, wh, stream);
-            if (rc) break;
-            float ms = 0.f;
-            if (cudaEventRecord(ev[1], s) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess ||
-                cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) {
-                rc = cuda_fail(cudaGetLastError(), "grid_autotune");
-                break;
-            }
-            ms /= repeats;
-            if (best < 0.f || ms < best) {
-                best = ms;
-                best_seg = seg_lens[i];
-                best_slots = slots[k];
-            }
+    wg_plan best_plan{w.seg_len, w.slots, w.fixed_r ? WG_PLAN_FIXED_R : 0, 0};
+    int rc = WG_OK;
+    for (const wg_plan& p : list) {
+        if ((rc = worklist_plan(wh, th, &p, stream))) break;
+        if ((rc = grid_vis(gh, th, wh, stream))) break;      // warm-up (occupancy query, caches)
+        if (cudaEventRecord(ev[0], s) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "grid_autotune");
+            break;
+        }
+        for (int r = 0; r < repeats && rc == WG_OK; ++r) rc = grid_vis(gh, th, wh, stream);
+        if (rc) break;
+        float ms = 0.f;
+        if (cudaEventRecord(ev[1], s) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "grid_autotune");
+            break;
+        }
+        ms /= repeats;
+        if (best < 0.f || ms < best) {
+            best = ms;
+            best_plan = p;
         }
     }
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
     if (rc) return rc;
-    if ((rc = worklist_plan(wh, th, best_seg, best_slots, stream))) return rc;
+    if ((rc = worklist_plan(wh, th, &best_plan, stream))) return rc;
     if ((rc = grid_zero(gh, stream))) return rc;
     WG_CUDA(cudaStreamSynchronize(s));
+    if (best_out) *best_out = best_plan;
     if (best_ms) *best_ms = best;
     return WG_OK;
 }

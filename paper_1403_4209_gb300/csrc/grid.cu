@@ -16,7 +16,7 @@
 // registers while the current record's FMAs run.  When the footprint moves, the lane recomputes
 // its offsets with the modular wrap and flushes the pixels that changed.  The segment's entries
 // and weighted visibilities are staged in shared memory once per task (cp.async).  R (points per
-// lane) is a template parameter, dispatched per run of records with the same support and channel.
+// lane) is chosen per run of records with the same support and channel, or fixed per launch.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -110,6 +110,30 @@ __device__ __forceinline__ TS load_sample(const TS* p)
     return v;
 }
 
+// A float2 sample is loaded straight into a 64-bit register pair; narrower samples are widened
+// and packed.
+__device__ __forceinline__ f32x2 load_kv(const float2* p) { return __ldg(reinterpret_cast<const f32x2*>(p)); }
+template <typename TS>
+__device__ __forceinline__ TS load_kv(const TS* p) { return load_sample(p); }
+template <typename TS>
+struct KvReg { typedef TS type; };
+template <>
+struct KvReg<float2> { typedef f32x2 type; };
+__device__ __forceinline__ f32x2 kv_x2(f32x2 v) { return v; }
+template <typename TS>
+__device__ __forceinline__ f32x2 kv_x2(TS v)
+{
+    const float2 f = to_f2(v);
+    return pack2(f.x, f.y);
+}
+
+// Accumulators per point and polarisation.  P = 1 keeps two packed pairs, A = k (gx, gx) and
+// B = k (gy, gy) summed over records, so that a loaded sample k = (kx, ky) feeds the packed FMAs
+// as it is; the pixel's sum is (A.x - B.y, A.y + B.x).  P = 2, 4 keep one pair, summed as
+// (gx, gy) (kx, kx) + (-gy, gx) (ky, ky): the two broadcasts of k per point serve P polarisations.
+template <int P>
+constexpr int acc_pairs() { return P == 1 ? 2 : 1; }
+
 // exact rounding error of s = fl(a + b) (TwoSum, Knuth)
 __device__ __forceinline__ float two_sum_err(float a, float b, float s)
 {
@@ -128,12 +152,19 @@ __device__ __forceinline__ float4 add_err4(float4 old, float4 v)
 // which the rounding error of the add is recovered exactly and added to the error grid.
 template <int P, bool COMP>
 __device__ __forceinline__ void flush_pixel(float2* __restrict__ gch, float2* __restrict__ ech, int pix,
-                                            f32x2 (&acc)[P])
+                                            f32x2 (&acc)[P][acc_pairs<P>()])
 {
     float2* d = gch + (size_t)pix * P;
     float2 a[P];
 #pragma unroll
-    for (int p = 0; p < P; ++p) a[p] = unpack2(acc[p]);
+    for (int p = 0; p < P; ++p) {
+        if constexpr (acc_pairs<P>() == 2) {
+            const float2 u = unpack2(acc[p][0]), v = unpack2(acc[p][1]);
+            a[p] = make_float2(u.x - v.y, u.y + v.x);
+        } else {
+            a[p] = unpack2(acc[p][0]);
+        }
+    }
     if constexpr (P == 1) {
         if constexpr (COMP) {
             const float2 o = atomicAdd(d, a[0]);
@@ -156,7 +187,9 @@ __device__ __forceinline__ void flush_pixel(float2* __restrict__ gch, float2* __
         }
     }
 #pragma unroll
-    for (int p = 0; p < P; ++p) acc[p] = 0ull;
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int q = 0; q < acc_pairs<P>(); ++q) acc[p][q] = 0ull;
 }
 
 // After staging, an entry's w field holds its key: support << 16 | channel, or -1 for an
@@ -165,14 +198,19 @@ __device__ __forceinline__ int entry_key(const int4& E) { return E.w; }
 
 // Processes records [j, e1) while their (support, channel) key equals `key` with R <= kRMax
 // points per lane (task block `blk` of the support's footprint); flushes its pixels and returns
-// the first record not processed.  R is warp-uniform: the unrolled point loops stop at R.
-template <int P, typename TS, bool COMP>
+// the first record not processed.  R is warp-uniform.  RT > 0 fixes R = RT at compile time (the
+// point loops then run without per-point checks; points past S^2 in the last block load sample
+// offset 0 and are never flushed); RT = 0 takes the runtime R and stops each loop at it.
+template <int P, typename TS, bool COMP, int RT>
 __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R, int blk, int N, int lane,
                                            WarpSmem<P>& sm, const TS* __restrict__ table,
                                            const int* __restrict__ supports, float2* __restrict__ gch,
                                            float2* __restrict__ ech)
 {
-    f32x2 acc[kRMax][P];
+    constexpr int KA = acc_pairs<P>();
+    typedef typename KvReg<TS>::type KV;
+    if constexpr (RT > 0) R = RT;
+    f32x2 acc[kRMax][P][KA];
     int toff[kRMax];
     unsigned valid = 0;
     const int s2 = S * S, sbase = blk * 32 * R;
@@ -187,14 +225,16 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
             sm.puv[r][lane] = (sl - pv * S) | (pv << 16);
         }
 #pragma unroll
-        for (int p = 0; p < P; ++p) acc[r][p] = 0ull;
+        for (int p = 0; p < P; ++p)
+#pragma unroll
+            for (int q = 0; q < KA; ++q) acc[r][p][q] = 0ull;
     }
     int fp = -1;             // footprint origin (x0 | y0 << 16) the offsets refer to
     bool pre = false;        // the current buffer holds the current record's samples (prefetched)
-    TS kva[kRMax], kvb[kRMax];     // raw samples, widened to float when used
+    KV kva[kRMax], kvb[kRMax];     // raw samples, widened to float when used
     // One record: load its samples unless prefetched, prefetch the next record's into `nxt` when
     // it keeps the footprint, then accumulate.  Returns false when the run ends at record j.
-    auto step = [&](TS (&cur_kv)[kRMax], TS (&nxt)[kRMax]) -> bool {
+    auto step = [&](KV (&cur_kv)[kRMax], KV (&nxt)[kRMax]) -> bool {
         if (j >= e1) return false;
         const int4 E = sm.rec[j].e;
         if (entry_key(E) != key) return false;
@@ -224,8 +264,8 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
             const TS* kz = table + E.z;
 #pragma unroll
             for (int r = 0; r < kRMax; ++r) {
-                if (r >= R) break;
-                cur_kv[r] = load_sample(kz + toff[r]);   // invalid points read offset 0, never flushed
+                if (RT == 0 && r >= R) break;
+                if (r < R) cur_kv[r] = load_kv(kz + toff[r]);   // invalid points read offset 0, never flushed
             }
         }
         pre = false;
@@ -235,27 +275,52 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
                 const TS* kz = table + E1.z;
 #pragma unroll
                 for (int r = 0; r < kRMax; ++r) {
-                    if (r >= R) break;
-                    nxt[r] = load_sample(kz + toff[r]);
+                    if (RT == 0 && r >= R) break;
+                    if (r < R) nxt[r] = load_kv(kz + toff[r]);
                 }
                 pre = true;
             }
         }
-        // acc += gamma * kv as (gx, gy) (kx, kx) + (-gy, gx) (ky, ky), two packed FMAs per pol
-        f32x2 g1[P], g2[P];
+        if constexpr (KA == 2) {
+            // A += k (gx, gx), B += k (gy, gy)
+            f32x2 gxx[P], gyy[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const float2 gm = sm.rec[j].g[p];
-            g1[p] = pack2(gm.x, gm.y);
-            g2[p] = pack2(-gm.y, gm.x);
-        }
+            for (int p = 0; p < P; ++p) {
+                const float2 gm = sm.rec[j].g[p];
+                gxx[p] = pack2(gm.x, gm.x);
+                gyy[p] = pack2(gm.y, gm.y);
+            }
 #pragma unroll
-        for (int r = 0; r < kRMax; ++r) {
-            if (r >= R) break;
-            const float2 kv = to_f2(cur_kv[r]);
-            const f32x2 kxx = pack2(kv.x, kv.x), kyy = pack2(kv.y, kv.y);
+            for (int r = 0; r < kRMax; ++r) {
+                if (RT == 0 && r >= R) break;
+                if (r < R) {
+                    const f32x2 k = kv_x2(cur_kv[r]);
 #pragma unroll
-            for (int p = 0; p < P; ++p) acc[r][p] = fma2(g2[p], kyy, fma2(g1[p], kxx, acc[r][p]));
+                    for (int p = 0; p < P; ++p) {
+                        acc[r][p][0] = fma2(k, gxx[p], acc[r][p][0]);
+                        acc[r][p][1] = fma2(k, gyy[p], acc[r][p][1]);
+                    }
+                }
+            }
+        } else {
+            // acc += gamma * kv as (gx, gy) (kx, kx) + (-gy, gx) (ky, ky), two packed FMAs per pol
+            f32x2 g1[P], g2[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float2 gm = sm.rec[j].g[p];
+                g1[p] = pack2(gm.x, gm.y);
+                g2[p] = pack2(-gm.y, gm.x);
+            }
+#pragma unroll
+            for (int r = 0; r < kRMax; ++r) {
+                if (RT == 0 && r >= R) break;
+                if (r < R) {
+                    const float2 kv = unpack2(kv_x2(cur_kv[r]));
+                    const f32x2 kxx = pack2(kv.x, kv.x), kyy = pack2(kv.y, kv.y);
+#pragma unroll
+                    for (int p = 0; p < P; ++p) acc[r][p][0] = fma2(g2[p], kyy, fma2(g1[p], kxx, acc[r][p][0]));
+                }
+            }
         }
         ++j;
         return true;
@@ -274,7 +339,7 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
 
 }  // namespace
 
-template <int P, typename TS, bool COMP>
+template <int P, typename TS, bool COMP, int RT>
 __global__ void __launch_bounds__(kWarps * 32, 4) k_grid(const int4* __restrict__ entries,
                                                          const float2* __restrict__ gamma,
                                                          const int* __restrict__ seg_off,
@@ -353,12 +418,12 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_grid(const int4* __restrict_
             float2* ech = COMP ? errgrid + (size_t)ch * chan_stride : nullptr;
             const int s2 = S * S;
             const int nb = (s2 + slots - 1) / slots;
-            const int R = (s2 + 32 * nb - 1) / (32 * nb);
+            const int R = RT > 0 ? RT : (s2 + 32 * nb - 1) / (32 * nb);
             if (blk >= nb) {     // this block has no points for this support: skip the run
                 while (j < n && entry_key(sm.rec[j].e) == key) ++j;
                 continue;
             }
-            j = run_records<P, TS, COMP>(j, n, key, S, R, blk, N, lane, sm, table, supports, gch, ech);
+            j = run_records<P, TS, COMP, RT>(j, n, key, S, R, blk, N, lane, sm, table, supports, gch, ech);
         }
     }
 }
@@ -382,7 +447,7 @@ __global__ void k_fold(float4* __restrict__ grid, float4* __restrict__ err, int6
     err[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-template <int P, typename TS, bool COMP>
+template <int P, typename TS, bool COMP, int RT>
 static int grid_launch(Grid& g, const Table& t, const WorkList& wl, const TS* table, cudaStream_t s)
 {
     // occupancy per segment length (the shared-memory staging grows with it)
@@ -390,29 +455,35 @@ static int grid_launch(Grid& g, const Table& t, const WorkList& wl, const TS* ta
     const int smem = (int)(kWarps * WarpSmem<P>::bytes(wl.seg_len));
     int& bps = blocks_per_sm[wl.seg_len / kSegLenMin];
     if (bps == 0) {
-        WG_CUDA(cudaFuncSetAttribute(k_grid<P, TS, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        WG_CUDA(cudaFuncSetAttribute(k_grid<P, TS, COMP, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)(kWarps * WarpSmem<P>::bytes(kSegLenMax))));
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_grid<P, TS, COMP>, kWarps * 32, smem) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_grid<P, TS, COMP, RT>, kWarps * 32, smem) !=
+                cudaSuccess ||
             bps < 1)
             bps = 1;
     }
-    k_grid<P, TS, COMP><<<num_sms() * bps, kWarps * 32, smem, s>>>(
+    k_grid<P, TS, COMP, RT><<<num_sms() * bps, kWarps * 32, smem, s>>>(
         wl.entries, wl.gamma, wl.seg_off, wl.scal, t.supports_d, table, g.data, g.err, g.n, t.K, g.n_chan,
         t.n_samples, wl.seg_len, wl.slots, wl.task_counter, wl.scal + 3);
     WG_LAUNCHED("k_grid");
     return WG_OK;
 }
 
+// The fixed-R kernels exist for FP32 tables without compensation, slots = 128 or 256.
 template <int P, bool COMP>
 static int grid_dispatch(Grid& g, const Table& t, const WorkList& wl, cudaStream_t s)
 {
     switch (t.store) {
         case WG_BF16:
-            return grid_launch<P, __nv_bfloat162, COMP>(g, t, wl, static_cast<const __nv_bfloat162*>(t.data_lp), s);
+            return grid_launch<P, __nv_bfloat162, COMP, 0>(g, t, wl, static_cast<const __nv_bfloat162*>(t.data_lp), s);
         case WG_F16:
-            return grid_launch<P, __half2, COMP>(g, t, wl, static_cast<const __half2*>(t.data_lp), s);
+            return grid_launch<P, __half2, COMP, 0>(g, t, wl, static_cast<const __half2*>(t.data_lp), s);
         default:
-            return grid_launch<P, float2, COMP>(g, t, wl, t.data, s);
+            if constexpr (!COMP) {
+                if (wl.fixed_r && wl.slots == 256) return grid_launch<P, float2, false, 8>(g, t, wl, t.data, s);
+                if (wl.fixed_r && wl.slots == 128) return grid_launch<P, float2, false, 4>(g, t, wl, t.data, s);
+            }
+            return grid_launch<P, float2, COMP, 0>(g, t, wl, t.data, s);
     }
 }
 

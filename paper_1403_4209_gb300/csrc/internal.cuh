@@ -94,6 +94,7 @@ struct WorkList {
     int64_t seg_cap = 0;
     int seg_len = kSegLenDefault;         // gridder plan: entries per segment
     int slots = kSlotsDefault;            // gridder plan: footprint points per task
+    bool fixed_r = false;                 // gridder plan: R = slots / 32 for every support
     // per record
     int4* rinfo = nullptr;
     uint8_t* rclass = nullptr;

@@ -218,7 +218,7 @@ def _flags(rows, C, P, frac, seed, device):
 
 def make(name: str, device: str = "cpu", flag_frac: float = 0.0, n_times: Optional[int] = None,
          n_chan: Optional[int] = None, n_baselines: Optional[int] = None,
-         chan_group: Optional[int] = None) -> Workload:
+         chan_group: Optional[int] = None, chan0: int = 0) -> Workload:
     """Build one of the named workloads.
 
     name: "w0_small"   : plain w=0 gridding, 32 stations in a 2 km disk, 496 baselines x 256
@@ -229,7 +229,8 @@ def make(name: str, device: str = "cpu", flag_frac: float = 0.0, n_times: Option
           "degrid_1k"  : 64 stations, 600 steps, 4 channels 120-180 MHz, 4 pols, N=1024, K=16.
           "batch_8k"   : 256 stations log-radial to 10 km, 1800 steps, 64 channels
                          50-350 MHz, 1 pol, N=8192, K=64, supports 9..129.
-    n_times / n_chan / n_baselines shrink a workload to a seeded slice of the same geometry.
+    n_times / n_chan / n_baselines shrink a workload to a seeded slice of the same geometry;
+    chan0 is the first channel of an n_chan slice.
     chan_group: vis, weight and flag become lists of [rows, chan_group, P] tensors, one per
     group of consecutive channels, each drawn with its own seed (seed + 7919 * group index);
     the (all-ones) weight tensor is shared by the groups."""
@@ -278,8 +279,8 @@ def make(name: str, device: str = "cpu", flag_frac: float = 0.0, n_times: Option
         uvw = np.ascontiguousarray(uvw.reshape(-1, 3))
     else:
         uvw = uvw_full
-    if n_chan is not None:
-        freq = freq[:n_chan]
+    if n_chan is not None or chan0:
+        freq = freq[chan0:None if n_chan is None else chan0 + n_chan]
     rows, C = uvw.shape[0], freq.shape[0]
     if chan_group is None:
         vis = visibilities(uvw, freq, sky, P, noise, seed, device=device)

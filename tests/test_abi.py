@@ -77,8 +77,10 @@ def test_errors_raise_in_python():
 def test_plan_limits_and_null_handles():
     assert C["WG_PLAN_SEG_LEN_MIN"] <= C["WG_PLAN_SEG_LEN_DEFAULT"] <= C["WG_PLAN_SEG_LEN_MAX"]
     assert C["WG_PLAN_SLOTS_MIN"] <= C["WG_PLAN_SLOTS_DEFAULT"] <= C["WG_PLAN_SLOTS_MAX"]
-    assert all(C[k] % 32 == 0 for k in C if k.startswith("WG_PLAN_"))
-    assert wg.lib.worklist_plan(None, None, 128, 256, None) == C["WG_E_INVALID_ARG"]
+    assert all(C[k] % 32 == 0 for k in C if k.startswith("WG_PLAN_S"))
+    assert ctypes.sizeof(_lib.Plan) == 16 and C["WG_PLAN_FIXED_R"] == 1
+    pl = _lib.Plan(128, 256, 0, 0)
+    assert wg.lib.worklist_plan(None, None, ctypes.byref(pl), None) == C["WG_E_INVALID_ARG"]
     assert "null" in _err()
-    assert wg.lib.worklist_get_plan(None, None, None) == C["WG_E_INVALID_ARG"]
-    assert wg.lib.grid_autotune(None, None, None, None, 0, None, 0, 3, None, None) == C["WG_E_INVALID_ARG"]
+    assert wg.lib.worklist_get_plan(None, None) == C["WG_E_INVALID_ARG"]
+    assert wg.lib.grid_autotune(None, None, None, None, 0, 3, None, None, None) == C["WG_E_INVALID_ARG"]

@@ -1,4 +1,5 @@
-"""Gridder plans (segment length x footprint points per task): every plan grids the same sums,
+"""Gridder plans (segment length x footprint points per task x per-support or fixed points per
+lane): every plan grids the same sums,
 the task count is the one the plan defines, and grid_autotune keeps a candidate plan and
 leaves the grid zeroed.
 
@@ -17,7 +18,8 @@ from gpu_common import max_rel, rel_l2, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
-PLANS = [(32, 64), (64, 128), (128, 256), (256, 192), (256, 256), (96, 160)]
+PLANS = [(32, 64, False), (64, 128, False), (128, 256, False), (256, 192, False), (256, 256, False),
+         (96, 160, False), (128, 256, True), (64, 128, True), (256, 256, True), (128, 192, True)]
 
 
 @pytest.fixture(scope="module")
@@ -33,12 +35,12 @@ def _tasks(entries, supports, seg_len, slots):
     return int(sum(nb[i:i + seg_len].max() for i in range(0, n, seg_len)))
 
 
-@pytest.mark.parametrize("seg_len,slots", PLANS)
-def test_plan_grids_the_same_sums(case, seg_len, slots):
+@pytest.mark.parametrize("seg_len,slots,fixed_r", PLANS)
+def test_plan_grids_the_same_sums(case, seg_len, slots, fixed_r):
     wl, ref, gpu = case
     g, t, batch, wlst = gpu["objects"]
-    wlst.plan(t, seg_len, slots)
-    assert wlst.plan_params == (seg_len, slots)
+    wlst.plan(t, seg_len, slots, fixed_r)
+    assert wlst.plan_params == (seg_len, slots, fixed_r)
     g.zero()
     wg.grid_vis(g, t, wlst)
     torch.cuda.synchronize()
@@ -61,8 +63,9 @@ def test_plan_rejects_bad_parameters(case):
 def test_autotune_keeps_a_candidate_and_zeroes_the_grid(case):
     wl, ref, gpu = case
     g, t, batch, wlst = gpu["objects"]
-    seg, slots, ms = wg.grid_autotune(g, t, wlst, seg_lens=[64, 128], slots=[128, 256], repeats=2)
-    assert seg in (64, 128) and slots in (128, 256) and ms > 0
+    cands = [(64, 128, False), (128, 256, True), (128, 256, False)]
+    seg, slots, fixed_r, ms = wg.grid_autotune(g, t, wlst, candidates=cands, repeats=2)
+    assert (seg, slots, fixed_r) in cands and ms > 0
     torch.cuda.synchronize()
     assert not torch.any(g.data != 0) and not torch.any(g.normaliser() != 0)
     wg.grid_vis(g, t, wlst)
@@ -70,5 +73,5 @@ def test_autotune_keeps_a_candidate_and_zeroes_the_grid(case):
     assert rel_l2(g.data.cpu().numpy(), ref["grid"]) < 1e-5
     # the plan carries over to the next batch prepared on this work list
     wg.vis_compress(g, t, batch, wlst)
-    assert wlst.plan_params == (seg, slots)
+    assert wlst.plan_params == (seg, slots, fixed_r)
     assert wlst.stats()["tasks"] == _tasks(gpu["entries"], t.supports, seg, slots)
