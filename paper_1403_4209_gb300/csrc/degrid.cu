@@ -2,8 +2,8 @@
 //
 // For a gridded entry (footprint origin (x0, y0), kernel pointer z, channel c) the kernel sum
 //   m_p = sum_{i,j} conj(C[z + i S + j]) grid_c,p(y0 + i, x0 + j)
-// is a gather: one warp per entry, lanes striding over the S x S footprint, a shuffle
-// reduction.  Compression (Sec. 4.3.3) carries over: every record compressed into the entry
+// is a gather: one warp per entry (chunks of consecutive entries per warp), lanes striding over
+// the S x S footprint, a shuffle reduction.  Compression (Sec. 4.3.3) carries over: every record compressed into the entry
 // has the same footprint and kernel samples, so m is computed once per run and written to each
 // record of the run, conjugated back where psi = -1 (w' < 0), and for the adjoint mode scaled
 // by eps (1 - f) (the vis -> grid map's R-linear outer factor).
@@ -11,96 +11,133 @@
 
 namespace wg {
 
+typedef unsigned long long f32x2;     // a packed FP32 pair (Blackwell f32x2 arithmetic)
+
+__device__ __forceinline__ f32x2 pack2(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ float2 unpack2(f32x2 v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// the P polarisations of one pixel as packed pairs
 template <int P>
-__device__ __forceinline__ void load_pixel(const float2* __restrict__ g, float2 (&v)[P])
+__device__ __forceinline__ void load_pixel(const float2* __restrict__ g, f32x2 (&v)[P])
 {
     if constexpr (P == 1) {
-        v[0] = __ldg(g);
-    } else if constexpr (P == 2) {
-        const float4 a = __ldg(reinterpret_cast<const float4*>(g));
-        v[0] = make_float2(a.x, a.y);
-        v[1] = make_float2(a.z, a.w);
+        v[0] = __ldg(reinterpret_cast<const f32x2*>(g));
     } else {
-        const float4 a = __ldg(reinterpret_cast<const float4*>(g));
-        const float4 b = __ldg(reinterpret_cast<const float4*>(g) + 1);
-        v[0] = make_float2(a.x, a.y);
-        v[1] = make_float2(a.z, a.w);
-        v[2] = make_float2(b.x, b.y);
-        v[3] = make_float2(b.z, b.w);
+#pragma unroll
+        for (int h = 0; h < P; h += 2) {
+            const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(g + h));
+            v[h] = a.x;
+            v[h + 1] = a.y;
+        }
     }
 }
 
+constexpr int kDegridChunk = 4;     // consecutive entries a warp takes from the counter at a time
+
+// A warp takes chunks of consecutive entries from a global counter, so that the overlapping
+// footprints of consecutive entries of a track are read by the same SM (L1 reuse).  Per entry
+// the lanes stride over the S x S footprint and accumulate conj(k) g as the packed pairs
+// A = (kx, kx) (gx, gy) and B = (ky, ky) (gx, gy): conj(k) g = (A.x + B.y, A.y - B.x).
 template <int P>
-__global__ void __launch_bounds__(256) k_degrid(const int4* __restrict__ entries, const int2* __restrict__ runs,
+__global__ void __launch_bounds__(256, 4) k_degrid(const int4* __restrict__ entries, const int2* __restrict__ runs,
                                                 const long long* __restrict__ scal, const int* __restrict__ supports,
                                                 const float2* __restrict__ table, const float2* __restrict__ grid,
                                                 int N, int C, const double* __restrict__ uvw,
                                                 const float* __restrict__ weight, const uint8_t* __restrict__ flag,
                                                 int adjoint, float2* __restrict__ out, int K, int64_t n_samples,
-                                                int64_t rows, long long* __restrict__ dropped)
+                                                int64_t rows, unsigned int* __restrict__ counter,
+                                                long long* __restrict__ dropped)
 {
     const long long n = scal[0];
     const int lane = threadIdx.x & 31;
-    const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long e = warp0; e < n; e += nwarps) {
-        const int4 E = entries[e];
-        const int k = E.w & 0xFFF, ch = (E.w >> 16) & 0xFFFF;
-        if (k >= K || ch >= C) {                 // device-side bounds checks (never taken)
-            if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
-            continue;
-        }
-        const int S = __ldg(&supports[k]);
-        const int x0 = E.x & 0xFFFF, y0 = (E.x >> 16) & 0xFFFF, z = E.z;
-        const int2 run = runs[e];
-        if (x0 + S > N || y0 + S > N || z < 0 || (int64_t)z + (int64_t)S * S > n_samples || run.x < 0 ||
-            run.y < run.x || (int64_t)run.y >= rows) {
-            if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
-            continue;
-        }
-        const float2* gch = grid + (size_t)ch * N * N * P;
-        float2 acc[P];
-#pragma unroll
-        for (int p = 0; p < P; ++p) acc[p] = make_float2(0.f, 0.f);
-        const int s2 = S * S;
-        int i = lane / S, j = lane - (lane / S) * S;
-        const int di = 32 / S, dj = 32 - di * S;
-        for (int s = lane; s < s2; s += 32) {
-            const float2 kv = __ldg(&table[z + s]);
-            float2 gv[P];
-            load_pixel<P>(gch + ((size_t)(y0 + i) * N + x0 + j) * P, gv);
-#pragma unroll
-            for (int p = 0; p < P; ++p) {   // conj(kv) * gv
-                acc[p].x = fmaf(kv.x, gv[p].x, fmaf(kv.y, gv[p].y, acc[p].x));
-                acc[p].y = fmaf(kv.x, gv[p].y, fmaf(-kv.y, gv[p].x, acc[p].y));
+    for (;;) {
+        unsigned int chunk = 0;
+        if (lane == 0) chunk = atomicAdd(counter, 1u);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        const long long c0 = (long long)chunk * kDegridChunk;
+        if (c0 >= n) break;
+        const long long c1 = min(n, c0 + kDegridChunk);
+        for (long long e = c0; e < c1; ++e) {
+            const int4 E = entries[e];
+            const int k = E.w & 0xFFF, ch = (E.w >> 16) & 0xFFFF;
+            if (k >= K || ch >= C) {                 // device-side bounds checks (never taken)
+                if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
+                continue;
             }
-            j += dj;
-            i += di;
-            if (j >= S) {
-                j -= S;
-                ++i;
+            const int S = __ldg(&supports[k]);
+            const int x0 = E.x & 0xFFFF, y0 = (E.x >> 16) & 0xFFFF, z = E.z;
+            const int2 run = runs[e];
+            if (x0 + S > N || y0 + S > N || z < 0 || (int64_t)z + (int64_t)S * S > n_samples || run.x < 0 ||
+                run.y < run.x || (int64_t)run.y >= rows) {
+                if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
+                continue;
             }
-        }
+            const float2* gch = grid + (size_t)ch * N * N * P;
+            f32x2 A[P], B[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
+            for (int p = 0; p < P; ++p) A[p] = B[p] = 0ull;
+            const int s2 = S * S;
+            int i = lane / S, j = lane - (lane / S) * S;
+            const int di = 32 / S, dj = 32 - di * S;
+            for (int s = lane; s < s2; s += 32) {
+                const float2 kv = __ldg(&table[z + s]);
+                const f32x2 kxx = pack2(kv.x, kv.x), kyy = pack2(kv.y, kv.y);
+                f32x2 gv[P];
+                load_pixel<P>(gch + ((size_t)(y0 + i) * N + x0 + j) * P, gv);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                acc[p].x += __shfl_xor_sync(0xffffffffu, acc[p].x, o);
-                acc[p].y += __shfl_xor_sync(0xffffffffu, acc[p].y, o);
+                for (int p = 0; p < P; ++p) {
+                    A[p] = fma2(kxx, gv[p], A[p]);
+                    B[p] = fma2(kyy, gv[p], B[p]);
+                }
+                j += dj;
+                i += di;
+                if (j >= S) {
+                    j -= S;
+                    ++i;
+                }
             }
-        }
-        for (int row = run.x + lane; row <= run.y; row += 32) {
-            const int64_t rec = (int64_t)row * C + ch;
-            const bool neg = uvw[3 * (int64_t)row + 2] < 0.0;
+            float2 acc[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                float2 v = neg ? make_float2(acc[p].x, -acc[p].y) : acc[p];
-                if (adjoint) {
-                    const float wf = weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
-                    v.x *= wf;
-                    v.y *= wf;
+                const float2 a = unpack2(A[p]), b = unpack2(B[p]);
+                acc[p] = make_float2(a.x + b.y, a.y - b.x);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    acc[p].x += __shfl_xor_sync(0xffffffffu, acc[p].x, o);
+                    acc[p].y += __shfl_xor_sync(0xffffffffu, acc[p].y, o);
                 }
-                out[rec * P + p] = v;
+            }
+            for (int row = run.x + lane; row <= run.y; row += 32) {
+                const int64_t rec = (int64_t)row * C + ch;
+                const bool neg = uvw[3 * (int64_t)row + 2] < 0.0;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    float2 v = neg ? make_float2(acc[p].x, -acc[p].y) : acc[p];
+                    if (adjoint) {
+                        const float wf = weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
+                        v.x *= wf;
+                        v.y *= wf;
+                    }
+                    out[rec * P + p] = v;
+                }
             }
         }
     }
@@ -111,10 +148,16 @@ static int degrid_impl(const Grid& g, const Table& t, const wg_vis_in& in, const
                        cudaStream_t s)
 {
     WG_CUDA(cudaMemsetAsync(out, 0, sizeof(float2) * (size_t)in.n_rows * in.n_chan * P, s));
-    const int blocks = num_sms() * 8;
+    WG_CUDA(cudaMemsetAsync(wl.task_counter + 1, 0, sizeof(unsigned int), s));
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0 &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_degrid<P>, 256, 0) != cudaSuccess ||
+         blocks_per_sm < 1))
+        blocks_per_sm = 1;
+    const int blocks = num_sms() * blocks_per_sm;
     k_degrid<P><<<blocks, 256, 0, s>>>(wl.entries, wl.runs, wl.scal, t.supports_d, t.data, g.data, g.n, in.n_chan,
                                        in.uvw, in.weight, in.flag, mode == WG_DEGRID_ADJOINT ? 1 : 0, out, t.K,
-                                       t.n_samples, in.n_rows, wl.scal + 3);
+                                       t.n_samples, in.n_rows, wl.task_counter + 1, wl.scal + 3);
     WG_LAUNCHED("k_degrid");
     return WG_OK;
 }
