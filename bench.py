@@ -40,15 +40,19 @@ WORKLOADS = {
                 "beta=8; FP32 table; compression on",
     "w0_small": "32 stations (2 km disk), 496 baselines x 256 steps at 10 s, 1 channel 150 MHz, 1 pol; "
                 "grid 512^2; w=0, support 7, beta=8; compression off",
+    "degrid_1k": "differentiable sky model: 1024^2 FP32 sky (4 channels x 4 pols; seeded point sources plus a "
+                 "Gaussian blob) -> degridding forward, chi^2 against noisy complex64 visibilities, hand-written "
+                 "adjoint gridding backward; 64 stations (3 km Gaussian), 2016 baselines x 600 steps at 6 s, "
+                 "4 channels 120-180 MHz, 16 sqrt(w)-spaced w-planes, supports 9..33, beta=8, compression on",
     "batch_8k": "256 stations (10 km log-radial), 32640 baselines x 1800 steps at 2 s, 64 channels 50-350 MHz, "
                 "1 pol, complex64; grid 8192^2 x 64 ch; 64 sqrt(w)-spaced w-planes, supports 9..129; beta=8; "
                 "FP32 table; compression on; 8 groups of 8 channels through one reused work list, the whole "
                 "step captured in one CUDA graph, gridder plan autotuned per group",
 }
 # bounded CPU samples of the same geometry (channels, time steps)
-CPU_SAMPLE = {"wproj_2k": (4, 1200), "w0_small": (1, 256), "batch_8k": (2, 40)}
-REF_SAMPLE = {"wproj_2k": (2, 360), "w0_small": (1, 256), "batch_8k": (1, 40)}
-COMPRESS = {"wproj_2k": True, "w0_small": False, "batch_8k": True}
+CPU_SAMPLE = {"wproj_2k": (4, 1200), "w0_small": (1, 256), "batch_8k": (2, 40), "degrid_1k": (1, 300)}
+REF_SAMPLE = {"wproj_2k": (2, 360), "w0_small": (1, 256), "batch_8k": (1, 40), "degrid_1k": (1, 60)}
+COMPRESS = {"wproj_2k": True, "w0_small": False, "batch_8k": True, "degrid_1k": True}
 CHAN_GROUP = {"batch_8k": 8}
 # gridder plans the autotuner tries (seg_len, slots, fixed R): on the batch for the single-grid
 # workloads, per channel group for the batched one
@@ -505,6 +509,133 @@ def run_batch(args, rank, world, local_rank):
     return line
 
 
+def _sky(C, P, N, seed):
+    """Seeded sky image [C][P][N][N]: point sources in the parallel hands plus a Gaussian blob."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    img = np.zeros((C, P, N, N), np.float32)
+    for _ in range(8):
+        y, x = rng.integers(N // 4, 3 * N // 4, 2)
+        img[:, [0, P - 1], y, x] += rng.uniform(0.1, 1.0)
+    yy, xx = np.mgrid[0:N, 0:N]
+    img[:, 0] += 0.3 * np.exp(-((xx - 0.55 * N) ** 2 + (yy - 0.45 * N) ** 2) / (N / 16.0) ** 2)
+    return img
+
+
+def run_autograd(args, rank, world, local_rank):
+    """Differentiation: one step = forward (degridding of the sky), chi^2, backward (adjoint
+    gridding), all through the autograd Function."""
+    import torch
+
+    import paper_1403_4209_gb300 as wg
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = "cuda:%d" % local_rank
+    wl = synth.make(args.workload, device=dev, n_chan=args.n_chan, n_times=args.n_times, chan0=args.chan0)
+    tab = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+    uvw_d = torch.as_tensor(wl.uvw, device=dev)
+    freq_d = torch.as_tensor(wl.freq, device=dev)
+    sm = wg.SkyModel(tab, uvw_d, freq_d, wl.weight, wl.flag, wl.n_grid, wl.du)
+    x = torch.as_tensor(_sky(wl.n_chan, wl.n_pol, wl.n_grid, 77), device=dev).requires_grad_(True)
+    v_obs = wl.vis
+    stream = torch.cuda.current_stream()
+
+    def step():
+        x.grad = None
+        loss = (sm(x) - v_obs).abs().pow(2).sum()
+        loss.backward()
+        return loss
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st_f = sm.wl_fwd.stats()
+    st_a = sm.wl_adj.stats()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.begin()
+    n0 = wg.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = wg.launch_count() - n0
+    clocks.end()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    # kernel times of the forward and backward halves
+    f0, f1, b1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    x.grad = None
+    f0.record(stream)
+    pred = sm(x)
+    f1.record(stream)
+    loss = (pred - v_obs).abs().pow(2).sum()
+    b0 = torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    loss.backward()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    t_fwd, t_bwd = f0.elapsed_time(f1), b0.elapsed_time(b1)
+    tot_f = st_f["updates"] + st_f["updates_saved"]
+    tot_a = st_a["updates"] + st_a["updates_saved"]
+    value = world * (tot_f + tot_a) / (ms * 1e-3) / 1e9
+    line = {
+        "metric": "gridding/degridding G grid-point updates/s and % roofline at stated grid error",
+        "value": round(value, 3),
+        "unit": "G grid-point updates/s (total rate: forward degridding + backward gridding, whole step)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "%s: %s" % (args.workload, WORKLOADS[args.workload]),
+                   "records_per_step": wl.rows * wl.n_chan, "l2": "inputs larger than L2 (no flush needed)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "rates": {"forward_ms": round(t_fwd, 3), "backward_ms": round(t_bwd, 3),
+                  "forward_total_G": round(tot_f / (t_fwd * 1e-3) / 1e9, 3),
+                  "backward_total_G": round(tot_a / (t_bwd * 1e-3) / 1e9, 3),
+                  "updates_total_forward": tot_f, "updates_total_backward": tot_a,
+                  "updates_real_forward": st_f["updates"], "updates_real_backward": st_a["updates"]},
+        "roofline": None,
+        "e2e": None,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_sample_autograd(args.workload, *CPU_SAMPLE[args.workload])
+    return line
+
+
+def cpu_sample_autograd(workload, n_chan, n_times):
+    """The FP64 oracle's chi^2 and gradient (forward model and adjoint) on a bounded sample."""
+    import numpy as np
+
+    import oracle
+    import synth
+    from oracle import model
+
+    wl = synth.make(workload, n_chan=n_chan, n_times=n_times)
+    ot = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+    img = _sky(wl.n_chan, wl.n_pol, wl.n_grid, 77).astype(np.float64)
+    t0 = time.perf_counter()
+    pl = oracle.place(wl.uvw, wl.freq, wl.du, wl.n_grid, ot, flag=wl.flag.numpy())
+    model.chi2_grad(pl, ot, img, wl.vis.numpy(), wl.taper_support)
+    dt = time.perf_counter() - t0
+    upd = 2 * int(np.sum(pl.S[pl.griddable].astype(np.int64) ** 2)) * wl.n_pol
+    return {"value": round(upd / dt / 1e9, 4), "unit": "G grid-point updates/s (total rate)", "cores": 1,
+            "kind": "oracle", "seconds": round(dt, 2),
+            "sample": "%s geometry, %d channel x %d time steps x %d baselines (%d records), FP64 oracle: "
+                      "placement, forward model and adjoint (chi^2 gradient), single thread" % (
+                          workload, n_chan, n_times, wl.n_baselines, wl.rows * wl.n_chan)}
+
+
 def cpu_sample(workload, n_chan, n_times):
     """The FP64 oracle (placement, compression, gridding) on a bounded sample, same geometry."""
     import numpy as np
@@ -606,7 +737,8 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
-    line = (run_batch if args.workload in CHAN_GROUP else run_ours)(args, rank, world, local_rank)
+    runner = run_batch if args.workload in CHAN_GROUP else run_autograd if args.workload == "degrid_1k" else run_ours
+    line = runner(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -224,11 +224,13 @@ typedef struct wg_stats {
  *   A3 compaction of gridded records into channel-major lists, segmented into tasks;
  *   A4 gamma = sum over each run of eps (1-f) psi-conj(vis) (eqs. "compress1",
  *      "conjugatetake"), FP32 (eps (1-f) = 1 with WG_PREP_UNWEIGHTED);
- *   A5 the normaliser terms and statistics, added into the grid's N_p and counters when
- *      grid_vis runs.
+ *   A5 the normaliser terms (eps (1-f) zeta, summed per run) and statistics, added into the
+ *      grid's N_p and counters when grid_vis runs.
  * `grid` supplies N and du; `table` the planes, supports and zeta.  The work list keeps
  * the results until the next call on it.
- * Errors: INVALID_ARG, SHAPE (n_chan/n_pol/du mismatch), CAPACITY, CUDA. */
+ * Errors: INVALID_ARG, SHAPE (n_chan/n_pol/du mismatch), CAPACITY (also when n_chan x
+ * (16 n_pol + 1) bytes exceed the 227 KB preparation tile, e.g. more than 3575 channels at
+ * n_pol = 4), CUDA. */
 int vis_compress(const wg_grid* grid, const wg_table* table, const wg_vis_in* in,
                  int32_t flags, wg_worklist* wl, void* stream);
 
@@ -238,7 +240,7 @@ int worklist_stats(const wg_worklist* wl, wg_stats* out, void* stream);
 /* Device views of the work list, for inspection and tests.  entries: int32 [n][4] with
  * {x0 | y0 << 16, (-x0 mod S) | (-y0 mod S) << 16, z, k | chan << 16}; gamma: complex64
  * [n][n_pol]; runs: int32 [n][2] first and last row of each gridded run; rec_class: uint8
- * per input record, bit0 = g, bit1 = c, bit2 = griddable.  *n_entries is read from the
+ * per input record, bit0 = g, bit1 = c, bit2 = griddable, bit3 = take-conjugate (w' < 0).  *n_entries is read from the
  * device (synchronises `stream`). */
 int worklist_view(const wg_worklist* wl, const int32_t** entries, const void** gamma,
                   const int32_t** runs, const uint8_t** rec_class, int64_t* n_entries,

@@ -287,7 +287,7 @@ int worklist_create(int64_t max_records, int32_t C, int32_t P, wg_worklist** out
     al((void**)&w.scal, sizeof(long long) * 8);
     al((void**)&w.chan_base, sizeof(int) * (C + 1));
     al((void**)&w.norm_priv, sizeof(double) * kNormSlots * C * P);
-    al((void**)&w.norm_batch, sizeof(double) * (C * P + 2 * C));
+    al((void**)&w.norm_batch, sizeof(double) * (C * P + 3 * C));
     al((void**)&w.stat_priv, sizeof(unsigned long long) * kNormSlots * ST_N);
     al((void**)&w.stats, sizeof(unsigned long long) * ST_N);
     al((void**)&w.task_counter, sizeof(unsigned int) * 4);

@@ -82,6 +82,7 @@ struct Table {
     int* supports_d = nullptr;            // C-2 supports [K]
     int* offsets_d = nullptr;             // C-2 offsets [K]
     double* wbounds_d = nullptr;          // [K] squared sqrt(w) midpoints between planes
+    float* wbounds_f = nullptr;           // [K] the same rounded to float
     float* zeta_f = nullptr;              // C-3 in FP32 (normaliser terms)
     std::vector<int> supports, offsets;   // host copies
     std::vector<double> pswf;             // Legendre coefficients of psi_0 (even degrees)
@@ -135,7 +136,10 @@ struct PlaceParams {
     const int* supports;
     const int* offsets;
     const double* wbounds;
+    const float* wbounds_f;               // wbounds rounded to float (monotone prefilter)
     const float* zeta_f;
+    int qlim;                             // beta (N/2 + 2): |q| beyond it is off the grid
+    int beta_log2;                        // log2(beta), or -1 when beta is not a power of two
 };
 
 int launch_prep(const Table& t, const Grid& g, const wg_vis_in& in, int flags, WorkList& wl,

@@ -116,7 +116,7 @@ extern "C" int grid_vis_noalloc(const wg_grid_view* view, const wg_table* th, co
     w.scal = cv.take<long long>(8);
     w.chan_base = cv.take<int>(C + 1);
     w.norm_priv = cv.take<double>((int64_t)kNormSlots * C * P);
-    w.norm_batch = cv.take<double>((int64_t)C * P + 2 * C);
+    w.norm_batch = cv.take<double>((int64_t)C * P + 3 * C);
     w.stat_priv = cv.take<unsigned long long>((int64_t)kNormSlots * ST_N);
     w.stats = cv.take<unsigned long long>(ST_N);
     w.task_counter = cv.take<unsigned int>(4);

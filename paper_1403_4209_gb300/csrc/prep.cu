@@ -5,14 +5,15 @@
 //   k_classify  (PreProcessUVW, Sec. 4.3.4): FP64 placement of each record (row, chan), its
 //               griddability, the compression indicator c (eq. "ci": same footprint origin
 //               and kernel pointer as the griddable predecessor (row-1, chan)), g = gd & !c,
-//               normaliser terms eps (1-f) zeta (eq. "normalizer") and statistics; a block
-//               scan of g in channel-major order gives each gridded record its rank inside
-//               the tile (Index Create and Filter, Algorithm "index").
+//               and statistics; a block scan of g in channel-major order gives each gridded
+//               record its rank inside the tile (Index Create and Filter, Algorithm "index").
 //   k_scan_tiles / k_finalize: per-channel exclusive scan of the tile counts and the
 //               channel bases, so gridded records land channel-major, row-ordered.
 //   k_compact   (Compress Index Generate + Compress and Weigh Visibilities, Algorithm
 //               "compressindex", eqs. "compress1"/"conjugatetake"): each gridded record
-//               walks its run of compressed successors and sums eps (1-f) psi-conj(vis).
+//               walks its run of compressed successors and sums eps (1-f) psi-conj(vis); the
+//               run's eps (1-f) times its sub-kernel's zeta gives the normaliser terms (eq.
+//               "normalizer"), summed by k_norm_sum.
 //   k_segments + k_seg_scan (Plan Create / Plan Analyse, Algorithm "plan"): gridded entries
 //               are cut into segments of seg_len entries; each segment needs one gridder task
 //               per block of `slots` footprint points of its largest support.  The plan can be
@@ -27,10 +28,12 @@ namespace wg {
 
 namespace {
 
-__device__ __forceinline__ long long floor_div(long long a, long long b)
+// floor(a / d) for d > 0; a shift when d = 2^sh (sh >= 1)
+__device__ __forceinline__ int floor_div32(int a, int d, int sh)
 {
-    long long q = a / b;
-    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    if (sh > 0 && (d == (1 << sh))) return a >> sh;
+    int q = a / d;
+    if ((a % d != 0) && (a < 0)) --q;
     return q;
 }
 
@@ -39,49 +42,132 @@ struct Placed {
     int S;
 };
 
-// Placement of one record, FP64, each operation rounded once (no contraction).
-__device__ __forceinline__ Placed place(const double* __restrict__ uvw, int64_t row, double lam_inv,
-                                        double sc, const uint8_t* __restrict__ flag, int64_t rec,
-                                        int P, const PlaceParams& pp)
+// One row's coordinates rounded to float, and its take-conjugate flag (w' < 0, decided on the
+// FP64 value).
+struct RowF {
+    float u, v, wa;     // fl32(u'), fl32(v'), fl32(|w'|)
+    int neg;
+};
+
+__device__ __forceinline__ RowF row_f(const double* __restrict__ uvw, int64_t row)
 {
-    Placed o;
-    o.info = make_int4(0, 0, 0, 0);
-    o.S = 0;
     const double up = uvw[3 * row], vp = uvw[3 * row + 1], wp = uvw[3 * row + 2];
-    double tu = __dmul_rn(up, sc), tv = __dmul_rn(vp, sc), w = __dmul_rn(wp, lam_inv);
-    const bool neg = wp < 0.0;
-    if (neg) {
-        tu = -tu;
-        tv = -tv;
-        w = -w;
-    }
-    o.info.w = neg ? (1 << kBitNeg) : 0;
-    const double qu = ceil(__dsub_rn(tu, 0.5)), qv = ceil(__dsub_rn(tv, 0.5));
-    if (!(fabs(qu) < 1099511627776.0) || !(fabs(qv) < 1099511627776.0)) return o;   // 2^40
-    const long long iqu = (long long)qu, iqv = (long long)qv, b = pp.beta;
-    const long long xc = floor_div(2 * iqu + b - 1, 2 * b), yc = floor_div(2 * iqv + b - 1, 2 * b);
-    const int fu = (int)(iqu - b * xc), fv = (int)(iqv - b * yc);
-    int k = 0;
-    if (pp.K > 1) {   // nearest plane in sqrt(w): k = number of b_1..b_{K-1} with w >= b_m
-        if (!(w < __ldg(&pp.wbounds[pp.K - 1]))) return o;   // beyond the last plane (or NaN)
+    const unsigned long long bw = __double_as_longlong(wp);
+    const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
+    RowF r;
+    r.u = __double2float_rn(up);
+    r.v = __double2float_rn(vp);
+    r.wa = __double2float_rn(__longlong_as_double(bw & kAbs));
+    r.neg = (bw >> 63) && (bw & kAbs) != 0 && (bw & kAbs) <= kInf;
+    return r;
+}
+
+// q = ceil(t - 1/2) from the float estimate tf of t = fl64(u' sc): decided when no integer lies
+// within the estimate's error bound of tf - 1/2.  |tf - t| <= |t| (3 + tiny) 2^-24 (three float
+// roundings), and tf - 1/2 adds |tf| 2^-24; the margin |tf| 2^-20 + 2^-40 covers both.
+__device__ __forceinline__ bool ceil_half_f(float tf, int& q)
+{
+    if (!(fabsf(tf) < 16777216.0f)) return false;              // large, infinite or NaN
+    const float d = __fsub_rn(tf, 0.5f);
+    const float c = ceilf(d);
+    const float e = fabsf(tf) * 9.5367431640625e-07f + 9.094947e-13f;   // 2^-20 |tf| + 2^-40
+    if (!(__fsub_rn(c, d) > e) || !(__fsub_rn(d, __fsub_rn(c, 1.0f)) > e)) return false;
+    q = (int)c;
+    return true;
+}
+
+// Placement decisions (q_u, q_v, plane k), FP64, each operation rounded once (no contraction).
+// Returns false when the record is not griddable by position or plane.
+__device__ __forceinline__ bool place_exact(const double* __restrict__ uvw, int64_t row, double lam_inv, double sc,
+                                            bool neg, const PlaceParams& pp, int& iqu, int& iqv, int& k)
+{
+    const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
+    const double up = uvw[3 * row], vp = uvw[3 * row + 1], wp = uvw[3 * row + 2];
+    // (-a) b = -(a b) exactly, so flipping the sign of the scale negates tu, tv and w exactly
+    const double scs = neg ? -sc : sc;
+    const double tu = __dmul_rn(up, scs), tv = __dmul_rn(vp, scs);
+    const double w = __dmul_rn(__longlong_as_double(__double_as_longlong(wp) & kAbs), lam_inv);
+    // a NaN position is not griddable (a NaN w fails the plane test below)
+    if ((__double_as_longlong(tu) & kAbs) > kInf || (__double_as_longlong(tv) & kAbs) > kInf) return false;
+    // q = ceil(t - 1/2), converted with rounding toward +infinity in one instruction; the
+    // conversion saturates (beyond qlim: off the grid)
+    iqu = __double2int_ru(__dsub_rn(tu, 0.5));
+    iqv = __double2int_ru(__dsub_rn(tv, 0.5));
+    k = 0;
+    if (pp.K > 1) {
+        // nearest plane in sqrt(w): k = number of b_1..b_{K-1} with b_m <= w, griddable if w < b_K.
+        // Compared first in FP32: float rounding is monotone, so fl(b) < fl(w) implies b < w and
+        // fl(b) > fl(w) implies b > w; only bounds with fl(b) == fl(w) are compared in FP64.
+        const float wf = __double2float_rn(w);
+        const float fbK = __ldg(&pp.wbounds_f[pp.K - 1]);
+        if (wf == fbK) {
+            if (!(w < __ldg(&pp.wbounds[pp.K - 1]))) return false;
+        } else if (!(wf < fbK)) {
+            return false;                                     // beyond the last plane (or NaN)
+        }
         int lo = 0, hi = pp.K - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (w >= __ldg(&pp.wbounds[mid - 1])) lo = mid; else hi = mid - 1;
+            if (__ldg(&pp.wbounds_f[mid - 1]) < wf) lo = mid; else hi = mid - 1;
         }
         k = lo;
+        while (k < pp.K - 1 && __ldg(&pp.wbounds_f[k]) == wf && w >= __ldg(&pp.wbounds[k])) ++k;
     }
+    return true;
+}
+
+// Placement of one record.  The cell (q_u, q_v) and the plane k are decided from float
+// estimates when the estimate's error bound cannot cross a rounding or plane boundary, which
+// gives the same decisions as the FP64 steps (place_exact) that every other record takes.
+__device__ __forceinline__ Placed place(const double* __restrict__ uvw, int64_t row, const RowF& rf, double lam_inv,
+                                        double sc, float lam_f, float sc_f, const uint8_t* __restrict__ flag,
+                                        int64_t rec, int P, const PlaceParams& pp)
+{
+    Placed o;
+    o.info = make_int4(0, 0, 0, rf.neg ? (1 << kBitNeg) : 0);
+    o.S = 0;
+    int iqu, iqv, k = 0;
+    bool fast = false;
+    {
+        const float scs = rf.neg ? -sc_f : sc_f;
+        fast = ceil_half_f(__fmul_rn(rf.u, scs), iqu) && ceil_half_f(__fmul_rn(rf.v, scs), iqv);
+        if (fast && pp.K > 1) {
+            // w = fl64(|w'| lam_inv) estimated as fl32(fl32(|w'|) fl32(lam_inv)); b_m <= w is
+            // decided when fl32(b_m) lies outside w_f +- 2^-20 w_f (covers the estimate's three
+            // roundings and the rounding of b_m to float)
+            const float wf = __fmul_rn(rf.wa, lam_f);
+            const float e = wf * 9.5367431640625e-07f;
+            const float lo_w = __fsub_rn(wf, e), hi_w = __fadd_rn(wf, e);
+            const float fbK = __ldg(&pp.wbounds_f[pp.K - 1]);
+            if (!(hi_w < fbK)) {
+                fast = false;            // near or beyond the last bound, infinite or NaN: exact steps
+            } else {
+                int lo = 0, hi = pp.K - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (__ldg(&pp.wbounds_f[mid - 1]) < lo_w) lo = mid; else hi = mid - 1;
+                }
+                k = lo;
+                if (k < pp.K - 1 && !(__ldg(&pp.wbounds_f[k]) > hi_w)) fast = false;
+            }
+        }
+    }
+    if (!fast && !place_exact(uvw, row, lam_inv, sc, rf.neg, pp, iqu, iqv, k)) return o;
+    if (iqu >= pp.qlim || iqu <= -pp.qlim || iqv >= pp.qlim || iqv <= -pp.qlim) return o;   // off the grid
+    const int b = pp.beta;
+    const int xc = floor_div32(2 * iqu + b - 1, 2 * b, pp.beta_log2 + 1);
+    const int yc = floor_div32(2 * iqv + b - 1, 2 * b, pp.beta_log2 + 1);
+    const int fu = iqu - b * xc, fv = iqv - b * yc;
     const int S = __ldg(&pp.supports[k]);
     const int h = (S - 1) / 2;
-    const long long x0 = pp.N / 2 + xc - h, y0 = pp.N / 2 + yc - h;
+    const int x0 = pp.N / 2 + xc - h, y0 = pp.N / 2 + yc - h;
     if (x0 < 0 || y0 < 0 || x0 + S - 1 > pp.N - 1 || y0 + S - 1 > pp.N - 1) return o;
     bool unflagged = false;
     for (int p = 0; p < P; ++p) unflagged |= (flag[rec * P + p] == 0);
     if (!unflagged) return o;
     const int sub = (fv - pp.lo) * pp.beta + (fu - pp.lo);
-    const int ix0 = (int)x0, iy0 = (int)y0;
-    const int cu = (S - ix0 % S) % S, cv = (S - iy0 % S) % S;
-    o.info.x = ix0 | (iy0 << 16);
+    const int cu = (S - x0 % S) % S, cv = (S - y0 % S) % S;
+    o.info.x = x0 | (y0 << 16);
     o.info.y = cu | (cv << 16);
     o.info.z = __ldg(&pp.offsets[k]) + sub * S * S;
     o.info.w |= k | (1 << kBitGd);
@@ -135,22 +221,24 @@ __device__ void block_exclusive_scan(int* a, int n, int* warp_tot)
 }  // namespace
 
 __global__ void k_chan_scale(const double* __restrict__ freq, int C, double beta_over_du, double* lam_inv,
-                             double* sc)
+                             double* sc, float* lam_f, float* sc_f)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
     const double li = __ddiv_rn(freq[c], 299792458.0);
+    const double s = __dmul_rn(li, beta_over_du);
     lam_inv[c] = li;
-    sc[c] = __dmul_rn(li, beta_over_du);
+    sc[c] = s;
+    lam_f[c] = __double2float_rn(li);
+    sc_f[c] = __double2float_rn(s);
 }
 
 template <int P>
 __global__ void __launch_bounds__(512) k_classify(const double* __restrict__ uvw, const double* __restrict__ lam_inv,
-                                                  const double* __restrict__ sc, const float* __restrict__ weight,
-                                                  const uint8_t* __restrict__ flag, int64_t rows, int rpb,
-                                                  PlaceParams pp, int4* __restrict__ rinfo,
+                                                  const double* __restrict__ sc, const float* __restrict__ lam_f,
+                                                  const float* __restrict__ sc_f, const uint8_t* __restrict__ flag,
+                                                  int64_t rows, int rpb, PlaceParams pp, int4* __restrict__ rinfo,
                                                   uint8_t* __restrict__ rclass, int* __restrict__ tile_cnt,
-                                                  double* __restrict__ norm_priv,
                                                   unsigned long long* __restrict__ stat_priv)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -162,23 +250,27 @@ __global__ void __launch_bounds__(512) k_classify(const double* __restrict__ uvw
     const int cap = rpb * C;
     int4* s_info = reinterpret_cast<int4*>(smem);
     int* s_scan = reinterpret_cast<int*>(s_info + cap);            // [cap + 1]
-    float* s_norm = reinterpret_cast<float*>(s_scan + cap + 1);    // [C * P]
-    unsigned char* s_gc = reinterpret_cast<unsigned char*>(s_norm + C * P);  // [cap]
+    RowF* s_row = reinterpret_cast<RowF*>(s_scan + cap + 1);       // [rpb + 1]: rows row0-1 ..
+    unsigned char* s_gc = reinterpret_cast<unsigned char*>(s_row + rpb + 1);  // [cap]
     __shared__ int warp_tot[32];
     __shared__ unsigned long long s_stat[ST_N];
 
-    for (int i = threadIdx.x; i < C * P; i += blockDim.x) s_norm[i] = 0.f;
     if (threadIdx.x < ST_N) s_stat[threadIdx.x] = 0ull;
+
+    // pass 0: each row's coordinates as floats, once for all its channels
+    for (int rr = threadIdx.x - 1; rr < nrows; rr += blockDim.x)
+        if (row0 + rr >= 0) s_row[rr + 1] = row_f(uvw, row0 + rr);
+    __syncthreads();
 
     // pass 1: placement
     for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
         const int rr = j / C, ch = j - rr * C;
         const int64_t row = row0 + rr, rec = row * C + ch;
-        s_info[j] = place(uvw, row, lam_inv[ch], sc[ch], flag, rec, P, pp).info;
+        s_info[j] = place(uvw, row, s_row[rr + 1], lam_inv[ch], sc[ch], lam_f[ch], sc_f[ch], flag, rec, P, pp).info;
     }
     __syncthreads();
 
-    // pass 2: compression indicator, g, normaliser terms, statistics
+    // pass 2: compression indicator, g, statistics
     unsigned long long n_gd = 0, n_g = 0, n_c = 0, u_g = 0, u_c = 0;
     for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
         const int rr = j / C, ch = j - rr * C;
@@ -189,28 +281,20 @@ __global__ void __launch_bounds__(512) k_classify(const double* __restrict__ uvw
         if (pp.compress && gd && row > 0) {
             int4 pinfo;
             if (rr > 0) pinfo = s_info[j - C];
-            else pinfo = place(uvw, row - 1, lam_inv[ch], sc[ch], flag, rec - C, P, pp).info;
+            else pinfo = place(uvw, row - 1, s_row[0], lam_inv[ch], sc[ch], lam_f[ch], sc_f[ch], flag, rec - C, P,
+                               pp).info;
             c = ((pinfo.w >> kBitGd) & 1) && pinfo.x == info.x && pinfo.z == info.z;
         }
         const int g = gd & (c ^ 1);
-        s_gc[j] = (unsigned char)(g | (c << 1) | (gd << 2));
+        s_gc[j] = (unsigned char)(g | (c << 1) | (gd << 2) | (((info.w >> kBitNeg) & 1) << 3));
         s_scan[ch * nrows + rr] = g;
         if (gd) {
-            const int k = info.w & 0xFFF;
-            const int S = __ldg(&pp.supports[k]);
-            const unsigned long long s2 = (unsigned long long)S * S;
+            const unsigned long long S = (unsigned long long)__ldg(&pp.supports[info.w & 0xFFF]);
             n_gd += 1;
             n_g += g;
             n_c += c;
-            u_g += g ? s2 : 0ull;
-            u_c += c ? s2 : 0ull;
-            const int sub = (info.z - __ldg(&pp.offsets[k])) / (S * S);
-            const float zeta = __ldg(&pp.zeta_f[k * pp.beta * pp.beta + sub]);
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const float wf = pp.unweighted ? 1.0f : weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
-                atomicAdd(&s_norm[ch * P + p], wf * zeta);
-            }
+            u_g += g ? S * S : 0ull;
+            u_c += c ? S * S : 0ull;
         }
     }
     // block statistics
@@ -242,11 +326,7 @@ __global__ void __launch_bounds__(512) k_classify(const double* __restrict__ uvw
     for (int ch = threadIdx.x; ch < C; ch += blockDim.x)
         tile_cnt[tile * C + ch] = s_scan[(ch + 1) * nrows] - s_scan[ch * nrows];
     const int slot = (int)(tile % kNormSlots);
-    for (int i = threadIdx.x; i < C * P; i += blockDim.x)
-        if (s_norm[i] != 0.f) atomicAdd(&norm_priv[(int64_t)slot * C * P + i], (double)s_norm[i]);
-    if (threadIdx.x == 0) {
-        s_stat[ST_RECORDS] = (unsigned long long)nrec;
-    }
+    if (threadIdx.x == 0) s_stat[ST_RECORDS] = (unsigned long long)nrec;
     __syncthreads();
     if (threadIdx.x < ST_TASKS && s_stat[threadIdx.x])
         atomicAdd(&stat_priv[slot * ST_N + threadIdx.x], s_stat[threadIdx.x]);
@@ -290,9 +370,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int* __restrict__ tile_cnt,
     if (threadIdx.x == 0) chan_total[ch] = carry;
 }
 
-template <int P>
-__global__ void k_finalize(int* __restrict__ chan_base, int C, const double* __restrict__ norm_priv,
-                           double* __restrict__ norm_batch, const unsigned long long* __restrict__ stat_priv,
+__global__ void k_finalize(int* __restrict__ chan_base, int C, const unsigned long long* __restrict__ stat_priv,
                            unsigned long long* __restrict__ stats, long long* __restrict__ scal)
 {
     if (threadIdx.x == 0) {
@@ -304,11 +382,6 @@ __global__ void k_finalize(int* __restrict__ chan_base, int C, const double* __r
         }
         chan_base[C] = (int)run;
         scal[0] = run;
-    }
-    for (int i = threadIdx.x; i < C * P; i += blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < kNormSlots; ++k) s += norm_priv[(int64_t)k * C * P + i];
-        norm_batch[i] = s;
     }
     for (int q = threadIdx.x; q < ST_TASKS; q += blockDim.x) {
         unsigned long long s = 0;
@@ -325,62 +398,203 @@ __device__ __forceinline__ float2 vis_value(const __half2* __restrict__ v, int64
     return make_float2(scale * f.x, scale * f.y);
 }
 
+// weighted value eps (1-f) psi-conj(vis) of polarisation p of record rec, and eps (1-f)
+template <typename VT>
+__device__ __forceinline__ float2 weighted(const VT* __restrict__ vis, const float* __restrict__ weight,
+                                          const uint8_t* __restrict__ flag, int64_t i, float scale, bool neg,
+                                          int unweighted, float& wf)
+{
+    wf = unweighted ? 1.0f : weight[i] * (1.0f - (float)flag[i]);
+    const float2 v = vis_value(vis, i, scale);
+    return make_float2(wf * v.x, (neg ? -1.f : 1.f) * (wf * v.y));
+}
+
+// The same for all P polarisations of record rec with vector loads (vis 16-byte, weight
+// 4P-byte and flag P-byte aligned).
+template <int P>
+__device__ __forceinline__ void weighted_vec(const float2* __restrict__ vis, const float* __restrict__ weight,
+                                             const uint8_t* __restrict__ flag, int64_t rec, float, bool neg,
+                                             int unweighted, float2 (&q)[P], float (&wf)[P])
+{
+    float2 v[P];
+    if constexpr (P == 1) {
+        v[0] = vis[rec];
+    } else {
+#pragma unroll
+        for (int h = 0; h < P; h += 2) {
+            const float4 a = *reinterpret_cast<const float4*>(vis + rec * P + h);
+            v[h] = make_float2(a.x, a.y);
+            v[h + 1] = make_float2(a.z, a.w);
+        }
+    }
+    float w[P];
+    unsigned f = 0;
+    if constexpr (P == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(weight + rec * 4);
+        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+        f = *reinterpret_cast<const unsigned*>(flag + rec * 4);
+    } else if constexpr (P == 2) {
+        const float2 a = *reinterpret_cast<const float2*>(weight + rec * 2);
+        w[0] = a.x; w[1] = a.y;
+        f = *reinterpret_cast<const unsigned short*>(flag + rec * 2);
+    } else {
+        w[0] = weight[rec];
+        f = flag[rec];
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        wf[p] = unweighted ? 1.0f : w[p] * (1.0f - (float)((f >> (8 * p)) & 0xFF));
+        q[p] = make_float2(wf[p] * v[p].x, (neg ? -1.f : 1.f) * (wf[p] * v[p].y));
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void weighted_vec(const __half2* __restrict__ vis, const float* __restrict__ weight,
+                                             const uint8_t* __restrict__ flag, int64_t rec, float scale, bool neg,
+                                             int unweighted, float2 (&q)[P], float (&wf)[P])
+{
+#pragma unroll
+    for (int p = 0; p < P; ++p) q[p] = weighted(vis, weight, flag, rec * P + p, scale, neg, unweighted, wf[p]);
+}
+
+// One block per tile.  Pass 1 reads the tile's griddable records in natural order (coalesced,
+// vector loads when aligned), keeps eps (1-f) psi-conj(vis) and eps (1-f) per polarisation in
+// shared memory (polarisation-major, conflict-free) and lists the tile's gridded records.
+// Pass 2: each listed record sums its run of compressed successors (same channel, following
+// rows) from shared memory in row order, continuing into the following tiles through global
+// memory when the run crosses the tile's end; it writes its entry, gamma and run, and adds
+// zeta(sub-kernel) x sum eps (1-f) to the normaliser (all records of a run share the
+// sub-kernel).
 template <int P, typename VT>
-__global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo, const VT* __restrict__ vis,
-                                                 const float* __restrict__ vis_scale,
+__global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo, const uint8_t* __restrict__ rclass,
+                                                 const VT* __restrict__ vis, const float* __restrict__ vis_scale,
                                                  const float* __restrict__ weight, const uint8_t* __restrict__ flag,
                                                  int64_t rows, int rpb, int C, const int* __restrict__ tile_off,
-                                                 const int* __restrict__ chan_base, const int* __restrict__ supports,
+                                                 const int* __restrict__ chan_base, PlaceParams pp,
                                                  int4* __restrict__ entries, float2* __restrict__ gamma,
-                                                 int2* __restrict__ runs, int64_t cap,
-                                                 long long* __restrict__ scal, int unweighted)
+                                                 int2* __restrict__ runs, int64_t cap_entries,
+                                                 double* __restrict__ norm_priv, long long* __restrict__ scal, int vec)
 {
+    extern __shared__ __align__(16) unsigned char smem[];
     const int64_t tile = blockIdx.x;
     const int64_t row0 = tile * rpb;
     const int nrows = (int)min((int64_t)rpb, rows - row0);
     const int nrec = nrows * C;
+    const int cap = rpb * C;
+    float2* s_q = reinterpret_cast<float2*>(smem);                        // [P][cap]
+    float* s_w = reinterpret_cast<float*>(s_q + (size_t)cap * P);         // [P][cap]
+    float* s_norm = s_w + (size_t)cap * P;                                // [C][P]
+    int* s_heads = reinterpret_cast<int*>(s_norm + (size_t)C * P);        // [cap]
+    uint8_t* s_cls = reinterpret_cast<uint8_t*>(s_heads + cap);           // [cap]
+    __shared__ int n_heads;
+    const int unweighted = pp.unweighted;
+
+    if (threadIdx.x == 0) n_heads = 0;
+    for (int i = threadIdx.x; i < C * P; i += blockDim.x) s_norm[i] = 0.f;
+    __syncthreads();
     for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
+        const int64_t rec = row0 * C + j;
+        const int cls = rclass[rec];
+        s_cls[j] = (uint8_t)cls;
+        if (!(cls & 4)) continue;                       // not griddable
+        if (cls & 1) s_heads[atomicAdd(&n_heads, 1)] = j;
+        const float scale = vis_scale ? vis_scale[j % C] : 1.0f;
+        const bool neg = (cls >> 3) & 1;
+        if (vec) {
+            float2 q[P];
+            float wf[P];
+            weighted_vec<P>(vis, weight, flag, rec, scale, neg, unweighted, q, wf);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                s_q[(size_t)p * cap + j] = q[p];
+                s_w[(size_t)p * cap + j] = wf[p];
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                float wf;
+                s_q[(size_t)p * cap + j] = weighted(vis, weight, flag, rec * P + p, scale, neg, unweighted, wf);
+                s_w[(size_t)p * cap + j] = wf;
+            }
+        }
+    }
+    __syncthreads();
+
+    const int nh = n_heads;
+    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+        const int j = s_heads[h];
         const int rr = j / C, ch = j - rr * C;
         const int64_t row = row0 + rr, rec = row * C + ch;
         const int4 info = rinfo[rec];
-        if (!((info.w >> kBitG) & 1)) continue;
         const int rank = (info.w >> 16) & 0xFFFF;
         const int dst = chan_base[ch] + tile_off[tile * C + ch] + rank;
-        const float scale = vis_scale ? vis_scale[ch] : 1.0f;
-        if (dst < 0 || (int64_t)dst >= cap) {   // cannot happen with a consistent scan
+        if (dst < 0 || (int64_t)dst >= cap_entries) {   // cannot happen with a consistent scan
             atomicAdd(reinterpret_cast<unsigned long long*>(&scal[3]), 1ull);
             continue;
         }
         float2 acc[P];
-        {
-            const float sg = ((info.w >> kBitNeg) & 1) ? -1.f : 1.f;
+        float wsum[P];
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const float wf = unweighted ? 1.0f : weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
-                const float2 v = vis_value(vis, rec * P + p, scale);
-                acc[p] = make_float2(wf * v.x, sg * (wf * v.y));
-            }
+        for (int p = 0; p < P; ++p) {
+            acc[p] = s_q[(size_t)p * cap + j];
+            wsum[p] = s_w[(size_t)p * cap + j];
         }
         int64_t last = row;
-        for (int64_t r2 = row + 1; r2 < rows; ++r2) {
-            const int64_t rc2 = r2 * C + ch;
-            const int4 i2 = rinfo[rc2];
-            if (!((i2.w >> kBitC) & 1)) break;
-            const float sg = ((i2.w >> kBitNeg) & 1) ? -1.f : 1.f;
+        int r2 = rr + 1;
+        for (; r2 < nrows; ++r2) {
+            const int j2 = r2 * C + ch;
+            if (!(s_cls[j2] & 2)) break;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const float wf = unweighted ? 1.0f : weight[rc2 * P + p] * (1.0f - (float)flag[rc2 * P + p]);
-                const float2 v = vis_value(vis, rc2 * P + p, scale);
-                acc[p].x += wf * v.x;
-                acc[p].y += sg * (wf * v.y);
+                const float2 q = s_q[(size_t)p * cap + j2];
+                acc[p].x += q.x;
+                acc[p].y += q.y;
+                wsum[p] += s_w[(size_t)p * cap + j2];
             }
-            last = r2;
+            last = row0 + r2;
+        }
+        if (r2 == nrows) {                              // the run may go on in the next tiles
+            const float scale = vis_scale ? vis_scale[ch] : 1.0f;
+            for (int64_t g2 = row0 + nrows; g2 < rows; ++g2) {
+                const int64_t rc2 = g2 * C + ch;
+                const int cls2 = rclass[rc2];
+                if (!(cls2 & 2)) break;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    float wf;
+                    const float2 q = weighted(vis, weight, flag, rc2 * P + p, scale, (cls2 >> 3) & 1, unweighted, wf);
+                    acc[p].x += q.x;
+                    acc[p].y += q.y;
+                    wsum[p] += wf;
+                }
+                last = g2;
+            }
         }
         const int k = info.w & 0xFFF;
         entries[dst] = make_int4(info.x, info.y, info.z, k | (ch << 16));
 #pragma unroll
         for (int p = 0; p < P; ++p) gamma[(int64_t)dst * P + p] = acc[p];
         runs[dst] = make_int2((int)row, (int)last);
+        const int S = __ldg(&pp.supports[k]);
+        const int sub = (info.z - __ldg(&pp.offsets[k])) / (S * S);
+        const float zeta = __ldg(&pp.zeta_f[k * pp.beta * pp.beta + sub]);
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+            if (wsum[p] != 0.f) atomicAdd(&s_norm[ch * P + p], zeta * wsum[p]);
+    }
+    __syncthreads();
+    const int slot = (int)(tile % kNormSlots);
+    for (int i = threadIdx.x; i < C * P; i += blockDim.x)
+        if (s_norm[i] != 0.f) atomicAdd(&norm_priv[(int64_t)slot * C * P + i], (double)s_norm[i]);
+}
+
+// N_p of the batch: the sum of the privatised per-slot partials
+__global__ void k_norm_sum(const double* __restrict__ norm_priv, int n, double* __restrict__ norm_batch)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < kNormSlots; ++k) s += norm_priv[(int64_t)k * n + i];
+        norm_batch[i] = s;
     }
 }
 
@@ -439,10 +653,16 @@ __global__ void __launch_bounds__(1024) k_seg_scan(const int* __restrict__ seg_n
     }
 }
 
-static size_t classify_smem(int rpb, int C, int P)
+static size_t classify_smem(int rpb, int C)
 {
     const size_t cap = (size_t)rpb * C;
-    return cap * sizeof(int4) + (cap + 1) * sizeof(int) + (size_t)C * P * sizeof(float) + cap + 16;
+    return cap * sizeof(int4) + (cap + 1) * sizeof(int) + (rpb + 1) * 16 + cap + 16;
+}
+
+static size_t compact_smem(int rpb, int C, int P)
+{
+    const size_t cap = (size_t)rpb * C;
+    return cap * P * (sizeof(float2) + sizeof(float)) + (size_t)C * P * sizeof(float) + cap * sizeof(int) + cap + 16;
 }
 
 template <int P>
@@ -477,42 +697,60 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
     pp.supports = t.supports_d;
     pp.offsets = t.offsets_d;
     pp.wbounds = t.wbounds_d;
+    pp.wbounds_f = t.wbounds_f;
+    pp.qlim = t.beta * (g.n / 2 + 2);
+    pp.beta_log2 = -1;
+    for (int b = 0; b < 16; ++b)
+        if (t.beta == (1 << b)) pp.beta_log2 = b;
     pp.zeta_f = t.zeta_f;
 
     double* lam_inv = reinterpret_cast<double*>(wl.norm_batch + (size_t)C * P);   // [C]
     double* sc = lam_inv + C;                                                     // [C]
+    float* lam_f = reinterpret_cast<float*>(sc + C);                              // [C]
+    float* sc_f = lam_f + C;                                                      // [C]
 
     WG_CUDA(cudaMemsetAsync(wl.norm_priv, 0, sizeof(double) * kNormSlots * C * P, s));
     WG_CUDA(cudaMemsetAsync(wl.stat_priv, 0, sizeof(unsigned long long) * kNormSlots * ST_N, s));
     WG_CUDA(cudaMemsetAsync(wl.stats, 0, sizeof(unsigned long long) * ST_N, s));
     WG_CUDA(cudaMemsetAsync(wl.scal, 0, sizeof(long long) * 4, s));
 
-    k_chan_scale<<<(C + 127) / 128, 128, 0, s>>>(in.freq_hz, C, pp.beta_over_du, lam_inv, sc);
+    k_chan_scale<<<(C + 127) / 128, 128, 0, s>>>(in.freq_hz, C, pp.beta_over_du, lam_inv, sc, lam_f, sc_f);
     WG_LAUNCHED("k_chan_scale");
     if (rows > 0) {
-        const size_t sm = classify_smem(rpb, C, P);
+        const size_t sm = classify_smem(rpb, C);
         if (sm > 48 * 1024) WG_CUDA(cudaFuncSetAttribute(k_classify<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_classify<P><<<(unsigned)n_tiles, 512, sm, s>>>(in.uvw, lam_inv, sc, in.weight, in.flag, rows, rpb, pp,
-                                                          wl.rinfo, wl.rclass, wl.tile_cnt, wl.norm_priv, wl.stat_priv);
+        k_classify<P><<<(unsigned)n_tiles, 512, sm, s>>>(in.uvw, lam_inv, sc, lam_f, sc_f, in.flag, rows, rpb, pp,
+                                                          wl.rinfo, wl.rclass, wl.tile_cnt, wl.stat_priv);
         WG_LAUNCHED("k_classify");
     }
     k_scan_tiles<<<C, 1024, 0, s>>>(wl.tile_cnt, n_tiles, C, wl.chan_base);
     WG_LAUNCHED("k_scan_tiles");
-    k_finalize<P><<<1, 256, 0, s>>>(wl.chan_base, C, wl.norm_priv, wl.norm_batch, wl.stat_priv, wl.stats, wl.scal);
+    k_finalize<<<1, 256, 0, s>>>(wl.chan_base, C, wl.stat_priv, wl.stats, wl.scal);
     WG_LAUNCHED("k_finalize");
     if (rows > 0) {
-        if (in.vis_dtype == WG_VIS_COMPLEX_HALF)
-            k_compact<P, __half2><<<(unsigned)n_tiles, 512, 0, s>>>(
-                wl.rinfo, reinterpret_cast<const __half2*>(in.vis), in.vis_scale, in.weight, in.flag, rows, rpb, C,
-                wl.tile_cnt, wl.chan_base, t.supports_d, wl.entries, wl.gamma, wl.runs, wl.cap, wl.scal,
-                pp.unweighted);
-        else
-            k_compact<P, float2><<<(unsigned)n_tiles, 512, 0, s>>>(
-                wl.rinfo, reinterpret_cast<const float2*>(in.vis), nullptr, in.weight, in.flag, rows, rpb, C,
-                wl.tile_cnt, wl.chan_base, t.supports_d, wl.entries, wl.gamma, wl.runs, wl.cap, wl.scal,
-                pp.unweighted);
+        const size_t sm = compact_smem(rpb, C, P);
+        const uintptr_t va = reinterpret_cast<uintptr_t>(in.vis), wa = reinterpret_cast<uintptr_t>(in.weight),
+                        fa = reinterpret_cast<uintptr_t>(in.flag);
+        const int vec = (va % 16 == 0) && (wa % (4 * P) == 0) && (fa % P == 0);
+        if (sm > 227 * 1024)
+            return fail(WG_E_CAPACITY, "%d channels x %d polarisations do not fit one preparation tile", C, P);
+        if (in.vis_dtype == WG_VIS_COMPLEX_HALF) {
+            if (sm > 48 * 1024)
+                WG_CUDA(cudaFuncSetAttribute(k_compact<P, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_compact<P, __half2><<<(unsigned)n_tiles, 512, sm, s>>>(
+                wl.rinfo, wl.rclass, reinterpret_cast<const __half2*>(in.vis), in.vis_scale, in.weight, in.flag, rows,
+                rpb, C, wl.tile_cnt, wl.chan_base, pp, wl.entries, wl.gamma, wl.runs, wl.cap, wl.norm_priv, wl.scal, 0);
+        } else {
+            if (sm > 48 * 1024)
+                WG_CUDA(cudaFuncSetAttribute(k_compact<P, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_compact<P, float2><<<(unsigned)n_tiles, 512, sm, s>>>(
+                wl.rinfo, wl.rclass, reinterpret_cast<const float2*>(in.vis), nullptr, in.weight, in.flag, rows, rpb,
+                C, wl.tile_cnt, wl.chan_base, pp, wl.entries, wl.gamma, wl.runs, wl.cap, wl.norm_priv, wl.scal, vec);
+        }
         WG_LAUNCHED("k_compact");
     }
+    k_norm_sum<<<1, 256, 0, s>>>(wl.norm_priv, C * P, wl.norm_batch);
+    WG_LAUNCHED("k_norm_sum");
     return launch_plan(t, wl, s);
 }
 

@@ -185,11 +185,13 @@ int free_table(Table& t)
     cudaFree(t.supports_d);
     cudaFree(t.offsets_d);
     cudaFree(t.wbounds_d);
+    cudaFree(t.wbounds_f);
     cudaFree(t.zeta_f);
     t.data = nullptr;
     t.zeta = nullptr;
     t.supports_d = t.offsets_d = nullptr;
     t.wbounds_d = nullptr;
+    t.wbounds_f = nullptr;
     t.zeta_f = nullptr;
     return WG_OK;
 }
@@ -211,6 +213,7 @@ static int finish_layout(Table& t)
         cudaMalloc(&t.supports_d, sizeof(int) * t.K) != cudaSuccess ||
         cudaMalloc(&t.offsets_d, sizeof(int) * t.K) != cudaSuccess ||
         cudaMalloc(&t.wbounds_d, sizeof(double) * t.K) != cudaSuccess ||
+        cudaMalloc(&t.wbounds_f, sizeof(float) * t.K) != cudaSuccess ||
         cudaMalloc(&t.zeta_f, sizeof(float) * t.K * t.beta * t.beta) != cudaSuccess) {
         cudaGetLastError();
         free_table(t);
@@ -227,6 +230,9 @@ static int finish_layout(Table& t)
             wb[m - 1] = t.w_max * (tm * tm);
         }
     WG_CUDA(cudaMemcpy(t.wbounds_d, wb.data(), sizeof(double) * t.K, cudaMemcpyHostToDevice));
+    std::vector<float> wbf(t.K);
+    for (int m = 0; m < t.K; ++m) wbf[m] = (float)wb[m];     // round to nearest
+    WG_CUDA(cudaMemcpy(t.wbounds_f, wbf.data(), sizeof(float) * t.K, cudaMemcpyHostToDevice));
     return WG_OK;
 }
 

@@ -31,8 +31,9 @@ def _check(wl, compress, n_k=0, n_k_oracle=None):
     gp = run_gpu(wl, compress=compress, n_k=n_k)
     o = run_oracle(wl, compress=compress, n_k=n_k_oracle)
     pl = o["pl"]
-    # per-record classification: bit0 g, bit1 c, bit2 griddable
+    # per-record classification: bit0 g, bit1 c, bit2 griddable, bit3 take-conjugate
     cls = gp["rec_class"]
+    assert np.array_equal((cls >> 3) & 1, (pl.psi < 0).astype(np.uint8))
     assert np.array_equal(cls & 1, o["g"].astype(np.uint8))
     assert np.array_equal((cls >> 1) & 1, o["c"].astype(np.uint8))
     assert np.array_equal((cls >> 2) & 1, pl.griddable.astype(np.uint8))
@@ -131,3 +132,54 @@ def test_plane_boundaries_bit_exact():
     gp, o = _check(wl, False)
     pl = o["pl"]
     assert not pl.griddable[1 + K - 1] and pl.griddable[1 + 3 * K - 1]   # b_K excluded, just below it included
+
+
+@pytest.mark.parametrize("K", [1, 7])
+def test_nonfinite_and_signed_zero_coordinates_bit_exact(K):
+    # NaN, +-inf, huge finite and signed-zero u, v, w: classification, take-conjugate bit,
+    # statistics and grid must match the oracle (placement decisions are exact on both sides)
+    import itertools
+    from oracle.place import plane_bounds
+    special = [np.nan, np.inf, -np.inf, 1e300, -1e300, 0.0, -0.0, 5.3, -7.9]
+    wvals = [np.nan, np.inf, -np.inf, -0.0, 0.0, 120.0, -120.0, 1e300]
+    uvw = np.array([(u, v, w) for u, v, w in itertools.product(special, special, wvals)], dtype=np.float64)
+    rows = uvw.shape[0]
+    w_max = 500.0
+    sup = [9, 9, 11, 11, 13, 13, 15][:K]
+    wl = synth.Workload("nonfinite", uvw, np.array([synth.C0]), torch.ones((rows, 1, 1), dtype=torch.complex64),
+                        torch.ones((rows, 1, 1)), torch.zeros((rows, 1, 1), dtype=torch.uint8), 256, 1.0, K,
+                        w_max if K > 1 else 0.0, 4, sup, 7, rows, 1)
+    with np.errstate(invalid="ignore", over="ignore"):
+        gp, o = _check(wl, False)
+    assert o["pl"].griddable.any() and not o["pl"].griddable.all()
+
+
+@pytest.mark.parametrize("du", [1.0, 0.7])
+def test_cell_boundaries_bit_exact(du):
+    # u', v' on the rounding boundaries of the oversampled lattice (t - 1/2 an integer, t = u' sc,
+    # sc = beta / du with f = c0) and up to 3 ulps either side: the cell and sub-cell must match
+    # the oracle bit for bit (the float estimate cannot decide these; the FP64 steps must)
+    beta = 8
+    sc = float(beta) / du
+    base = (np.arange(-60, 60) + 0.5) / sc
+    vals = [base]
+    x = base.copy()
+    y = base.copy()
+    for _ in range(3):
+        x = np.nextafter(x, np.inf)
+        y = np.nextafter(y, -np.inf)
+        vals += [x.copy(), y.copy()]
+    u = np.concatenate(vals)
+    rng = np.random.default_rng(11)
+    v = rng.permutation(u)
+    rows = u.size
+    uvw = np.stack([u, v, rng.uniform(-5, 5, rows)], 1)
+    wl = synth.Workload("cell_edges", uvw, np.array([synth.C0]), torch.ones((rows, 1, 1), dtype=torch.complex64),
+                        torch.ones((rows, 1, 1)), torch.zeros((rows, 1, 1), dtype=torch.uint8), 64, du, 1, 0.0,
+                        beta, [7], 7, rows, 1)
+    gp, o = _check(wl, False)
+    pl = o["pl"]
+    assert pl.griddable.sum() > rows // 2
+    # the entries carry the sub-cell through z: compare it with the oracle's directly
+    g = np.nonzero(pl.griddable)[0]
+    assert np.array_equal(np.sort(gp["entries"][:, 2]), np.sort(pl.z[g]))
