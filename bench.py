@@ -50,7 +50,9 @@ WORKLOADS = {
                 "step captured in one CUDA graph, gridder plan autotuned per group",
 }
 # bounded CPU samples of the same geometry (channels, time steps)
-CPU_SAMPLE = {"wproj_2k": (4, 1200), "w0_small": (1, 256), "batch_8k": (2, 40), "degrid_1k": (1, 300)}
+CPU_SAMPLE = {"wproj_2k": (16, 1200), "w0_small": (1, 256), "batch_8k": (2, 40), "degrid_1k": (1, 300)}
+# worker processes of the CPU baseline (one channel each) where the oracle's table build is cheap
+CPU_PROCS = {"wproj_2k": 16}
 REF_SAMPLE = {"wproj_2k": (2, 360), "w0_small": (1, 256), "batch_8k": (1, 40), "degrid_1k": (1, 60)}
 COMPRESS = {"wproj_2k": True, "w0_small": False, "batch_8k": True, "degrid_1k": True}
 CHAN_GROUP = {"batch_8k": 8}
@@ -142,6 +144,30 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(inside)}
 
 
+def barrier(world):
+    """All ranks meet (no-op on one rank)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value, world, device="cpu"):
+    """The largest of every rank's value (the slowest rank's time), on every rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ms, world):
+    """Replicas: every rank processes the same units; the job's rate is all ranks' units over
+    the slowest rank's time, in 1e9 units per second."""
+    return world * units_per_rank / (ms * 1e-3) / 1e9
+
+
 def _gridder_traffic(per_launch_units):
     """DRAM bytes per k_grid launch from the committed ncu summary, scaled to this launch's
     gridded updates; None if the gridder source changed since the counters were taken."""
@@ -185,10 +211,15 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     ev_g = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
 
+    ev_p = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
     def step(k=None):
         g.zero()
+        if k is not None:
+            ev_p[k][0].record(stream)
         wg.vis_compress(g, tab, batch, wlst, compress=compress)
         if k is not None:
+            ev_p[k][1].record(stream)
             ev_g[k][0].record(stream)
         wg.grid_vis(g, tab, wlst)
         if k is not None:
@@ -206,8 +237,7 @@ def run_ours(args, rank, world, local_rank):
         step()
     torch.cuda.synchronize()
     st = wlst.stats()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     torch.cuda.synchronize()
     clocks.begin()
     n0 = wg.launch_count()
@@ -222,14 +252,12 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     t_grid = sum(a.elapsed_time(b) for a, b in ev_g) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        torch.distributed.barrier()
+    t_prep = sum(a.elapsed_time(b) for a, b in ev_p) / args.steps
+    ms = max_over_ranks(ms, world, dev)
+    barrier(world)
     real = st["updates"]
     total = st["updates"] + st["updates_saved"]
-    value = world * total / (ms * 1e-3) / 1e9
+    value = whole_job_rate(total, ms, world)
 
     # precision variants (reduced-precision tables, half visibilities, compensated flushes)
     variants = {}
@@ -325,8 +353,7 @@ def run_ours(args, rank, world, local_rank):
 
     e2e_run(2)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ne = max(3, args.steps // 2)
     x0.record(stream)
@@ -334,10 +361,7 @@ def run_ours(args, rank, world, local_rank):
     x1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = x0.elapsed_time(x1) / ne
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(ms_e2e, world, dev)
 
     peaks, src = _peaks()
     props = torch.cuda.get_device_properties(local_rank)
@@ -367,6 +391,12 @@ def run_ours(args, rank, world, local_rank):
                   "degrid_G": round(total / (t_degrid * 1e-3) / 1e9, 3),
                   "gridder_ms": round(t_grid, 4), "degrid_ms": round(t_degrid, 4),
                   "records_gridded": st["gridded"], "records_compressed": st["compressed"],
+                  "record_rate_real_M": round(st["gridded"] / (t_grid * 1e-3) / 1e6, 1),
+                  "record_rate_total_M": round(st["griddable"] / (t_grid * 1e-3) / 1e6, 1),
+                  "compression_ratio_records": round(st["compressed"] / max(1, st["gridded"]), 3),
+                  "compression_ratio_updates": round(st["updates_saved"] / max(1, st["updates"]), 3),
+                  "prep_ms": round(t_prep, 4),
+                  "prep_record_rate_M": round(st["records"] / (t_prep * 1e-3) / 1e6, 1),
                   "updates_real": real, "updates_total": total},
         "roofline": {"kernel": "k_grid", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
@@ -375,14 +405,17 @@ def run_ours(args, rank, world, local_rank):
                                     % (props.multi_processor_count, sm_mhz, src),
                      "traffic": traffic},
         "variants": variants,
-        "e2e": {"value": round(world * total / (ms_e2e * 1e-3) / 1e9, 3), "unit": "G grid-point updates/s",
+        "e2e": {"value": round(whole_job_rate(total, ms_e2e, world), 3), "unit": "G grid-point updates/s",
                 "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "pipelining": "inputs double-buffered on a copy stream"},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_sample(args.workload, *CPU_SAMPLE[args.workload])
+        nc, nt = CPU_SAMPLE[args.workload]
+        procs = min(CPU_PROCS.get(args.workload, 1), os.cpu_count() or 1, nc)
+        line["cpu_baseline"] = cpu_sample(args.workload, nc if procs > 1 else min(nc, 4), nt, procs)
+        line["grid_error"] = grid_error_sample(args.workload, dev, plan)
     return line
 
 
@@ -449,8 +482,7 @@ def run_batch(args, rank, world, local_rank):
     for _ in range(args.warmup):
         graph.replay()
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     torch.cuda.synchronize()
     clocks.begin()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -462,11 +494,8 @@ def run_batch(args, rank, world, local_rank):
     clocks.end()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * total / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(ms, world, dev)
+    value = whole_job_rate(total, ms, world)
     peaks, src = _peaks()
     props = torch.cuda.get_device_properties(local_rank)
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -554,8 +583,7 @@ def run_autograd(args, rank, world, local_rank):
     torch.cuda.synchronize()
     st_f = sm.wl_fwd.stats()
     st_a = sm.wl_adj.stats()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     torch.cuda.synchronize()
     clocks.begin()
     n0 = wg.launch_count()
@@ -569,10 +597,7 @@ def run_autograd(args, rank, world, local_rank):
     clocks.end()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     # kernel times of the forward and backward halves
     f0, f1, b1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     x.grad = None
@@ -588,7 +613,7 @@ def run_autograd(args, rank, world, local_rank):
     t_fwd, t_bwd = f0.elapsed_time(f1), b0.elapsed_time(b1)
     tot_f = st_f["updates"] + st_f["updates_saved"]
     tot_a = st_a["updates"] + st_a["updates_saved"]
-    value = world * (tot_f + tot_a) / (ms * 1e-3) / 1e9
+    value = whole_job_rate(tot_f + tot_a, ms, world)
     line = {
         "metric": "gridding/degridding G grid-point updates/s and % roofline at stated grid error",
         "value": round(value, 3),
@@ -636,15 +661,22 @@ def cpu_sample_autograd(workload, n_chan, n_times):
                           workload, n_chan, n_times, wl.n_baselines, wl.rows * wl.n_chan)}
 
 
-def cpu_sample(workload, n_chan, n_times):
-    """The FP64 oracle (placement, compression, gridding) on a bounded sample, same geometry."""
+def _oracle_setup(workload, chans, n_times):
+    """Inputs (one channel each) and the oracle's table for the CPU sample (untimed)."""
+    import oracle
+    import synth
+    sets = [synth.make(workload, n_chan=1, chan0=c, n_times=n_times) for c in chans]
+    wl = sets[0]
+    ot = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+    return sets, ot
+
+
+def _oracle_run(workload, wl, ot):
+    """The FP64 oracle (placement, compression, gridding) on one channel; returns (total updates,
+    start, end) on the host's monotonic clock."""
     import numpy as np
 
     import oracle
-    import synth
-
-    wl = synth.make(workload, n_chan=n_chan, n_times=n_times)
-    ot = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
     vis, w, f = wl.vis.numpy(), wl.weight.numpy(), wl.flag.numpy()
     t0 = time.perf_counter()
     pl = oracle.place(wl.uvw, wl.freq, wl.du, wl.n_grid, ot, flag=f)
@@ -654,14 +686,87 @@ def cpu_sample(workload, n_chan, n_times):
     else:
         g, c = pl.griddable, np.zeros_like(pl.griddable)
         oracle.grid_plain(pl, ot, vis, w, f, wl.n_grid)
-    dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
     st = oracle.stats(pl, g, c)
-    total = (st["updates"] + st["updates_saved"]) * wl.n_pol
-    return {"value": round(total / dt / 1e9, 4), "unit": "G grid-point updates/s (total rate)", "cores": 1,
-            "kind": "oracle", "seconds": round(dt, 2),
+    return (st["updates"] + st["updates_saved"]) * wl.n_pol, t0, t1
+
+
+def _oracle_proc(workload, chans, n_times, start, q):
+    """One worker of the all-core CPU baseline: set up its channels, wait for the others, run."""
+    import threading
+    sets, ot = _oracle_setup(workload, chans, n_times)
+    try:
+        start.wait(timeout=600)
+    except threading.BrokenBarrierError:
+        pass
+    for wl in sets:
+        q.put(_oracle_run(workload, wl, ot) + (wl.n_baselines, wl.rows))
+
+
+def cpu_sample(workload, n_chan, n_times, procs=1):
+    """The FP64 oracle on a bounded sample of the same geometry: n_chan channels x n_times steps.
+    procs > 1 spreads the channels over worker processes (spawned, so no CUDA state is
+    inherited) that start their timed sections together; the all-core rate is all updates over
+    the span of the timed sections, the single-core rate the mean over channels."""
+    if procs <= 1:
+        sets, ot = _oracle_setup(workload, range(n_chan), n_times)
+        res = [_oracle_run(workload, wl, ot) for wl in sets]
+        upd = sum(r[0] for r in res)
+        dt = sum(r[2] - r[1] for r in res)
+        return {"value": round(upd / dt / 1e9, 4), "unit": "G grid-point updates/s (total rate)",
+                "cores": 1, "kind": "oracle", "seconds": round(dt, 2),
+                "sample": "%s geometry, %d channels x %d time steps x %d baselines (%d records), FP64 oracle: "
+                          "placement + compression + gridding, single thread" % (
+                              workload, n_chan, n_times, sets[0].n_baselines, sets[0].rows * n_chan)}
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    start = ctx.Barrier(procs)
+    ps = [ctx.Process(target=_oracle_proc, args=(workload, list(range(i, n_chan, procs)), n_times, start, q))
+          for i in range(procs)]
+    for p in ps:
+        p.start()
+    res = [q.get(timeout=900) for _ in range(n_chan)]
+    for p in ps:
+        p.join(60)
+    upd = sum(r[0] for r in res)
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    single = sum(r[0] / (r[2] - r[1]) for r in res) / len(res)
+    return {"value": round(upd / span / 1e9, 4), "unit": "G grid-point updates/s (total rate)", "cores": procs,
+            "kind": "oracle", "seconds": round(span, 2), "single_core_value": round(single / 1e9, 4),
             "sample": "%s geometry, %d channels x %d time steps x %d baselines (%d records), FP64 oracle: "
-                      "placement + compression + gridding, single thread" % (
-                          workload, n_chan, n_times, wl.n_baselines, wl.rows * wl.n_chan)}
+                      "placement + compression + gridding, channels spread over %d processes" % (
+                          workload, n_chan, n_times, res[0][3], sum(r[4] for r in res), procs)}
+
+
+def grid_error_sample(workload, dev, plan):
+    """Grid error of the CUDA path against the FP64 oracle (plain definition, eq. "gridding") on a
+    seeded slice of the workload (300 baselines x 24 steps x 2 channels), with the bench's plan."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1403_4209_gb300 as wg
+    import synth
+    wl = synth.make(workload, n_chan=2, n_times=24, n_baselines=300)
+    tab = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+    g = wg.Grid(wl.n_grid, wl.du, wl.n_pol, wl.n_chan, device=dev)
+    b = wg.VisBatch(torch.as_tensor(wl.uvw, device=dev), torch.as_tensor(wl.freq, device=dev), wl.vis.to(dev),
+                    wl.weight.to(dev), wl.flag.to(dev))
+    w = wg.WorkList(wl.rows * wl.n_chan, wl.n_chan, wl.n_pol)
+    wg.vis_compress(g, tab, b, w, compress=COMPRESS[workload])
+    w.plan(tab, *plan)
+    wg.grid_vis(g, tab, w)
+    got = g.data.cpu().numpy()
+    ot = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+    f = wl.flag.numpy()
+    pl = oracle.place(wl.uvw, wl.freq, wl.du, wl.n_grid, ot, flag=f)
+    ref = oracle.grid_plain(pl, ot, wl.vis.numpy(), wl.weight.numpy(), f, wl.n_grid)
+    return {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "max_abs_over_max": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+            "reference": "FP64 oracle, plain gridding definition",
+            "sample": "%s geometry, 300 baselines x 24 steps x 2 channels (%d records)" % (workload,
+                                                                                      wl.rows * wl.n_chan)}
 
 
 def run_reference(args):
