@@ -40,6 +40,10 @@ WORKLOADS = {
                 "beta=8; FP32 table; compression on",
     "w0_small": "32 stations (2 km disk), 496 baselines x 256 steps at 10 s, 1 channel 150 MHz, 1 pol; "
                 "grid 512^2; w=0, support 7, beta=8; compression off",
+    "mfs_2k": "channel interleaving onto one grid (multi-frequency synthesis): the wproj_2k geometry (2016 "
+              "baselines x 3600 steps at 1 s, 4 pols) with 16 channels 12.2 kHz apart from 150 MHz; grid 2048^2 x 1; "
+              "32 sqrt(w)-spaced w-planes, supports 9..65; beta=8; FP32 table; compression over the natural "
+              "record order",
     "degrid_1k": "differentiable sky model: 1024^2 FP32 sky (4 channels x 4 pols; seeded point sources plus a "
                  "Gaussian blob) -> degridding forward, chi^2 against noisy complex64 visibilities, hand-written "
                  "adjoint gridding backward; 64 stations (3 km Gaussian), 2016 baselines x 600 steps at 6 s, "
@@ -50,11 +54,14 @@ WORKLOADS = {
                 "step captured in one CUDA graph, gridder plan autotuned per group",
 }
 # bounded CPU samples of the same geometry (channels, time steps)
-CPU_SAMPLE = {"wproj_2k": (16, 1200), "w0_small": (1, 256), "batch_8k": (2, 40), "degrid_1k": (1, 300)}
+CPU_SAMPLE = {"wproj_2k": (16, 1200), "w0_small": (1, 256), "batch_8k": (2, 40), "degrid_1k": (1, 300),
+              "mfs_2k": (4, 1200)}
 # worker processes of the CPU baseline (one channel each) where the oracle's table build is cheap
 CPU_PROCS = {"wproj_2k": 16}
 REF_SAMPLE = {"wproj_2k": (2, 360), "w0_small": (1, 256), "batch_8k": (1, 40), "degrid_1k": (1, 60)}
-COMPRESS = {"wproj_2k": True, "w0_small": False, "batch_8k": True, "degrid_1k": True}
+COMPRESS = {"wproj_2k": True, "w0_small": False, "batch_8k": True, "degrid_1k": True, "mfs_2k": True}
+# channel interleaving: every channel onto one grid, compression in natural record order
+INTERLEAVE = {"mfs_2k": True}
 CHAN_GROUP = {"batch_8k": 8}
 # gridder plans the autotuner tries (seg_len, slots, fixed R): on the batch for the single-grid
 # workloads, per channel group for the batched one
@@ -201,12 +208,14 @@ def run_ours(args, rank, world, local_rank):
     dev = "cuda:%d" % local_rank
     wl = synth.make(args.workload, device=dev, n_chan=args.n_chan, n_times=args.n_times, chan0=args.chan0)
     tab = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
-    g = wg.Grid(wl.n_grid, wl.du, wl.n_pol, wl.n_chan, device=dev)
+    inter = INTERLEAVE.get(args.workload, False)
+    gc = 1 if inter else wl.n_chan                         # grid channels
+    g = wg.Grid(wl.n_grid, wl.du, wl.n_pol, gc, device=dev)
     uvw_d = torch.as_tensor(wl.uvw, device=dev)
     freq_d = torch.as_tensor(wl.freq, device=dev)
     batch = wg.VisBatch(uvw_d, freq_d, wl.vis, wl.weight, wl.flag)
     wlst = wg.WorkList(wl.rows * wl.n_chan, wl.n_chan, wl.n_pol)
-    img = torch.empty((wl.n_chan, wl.n_grid, wl.n_grid), dtype=torch.float32, device=dev)
+    img = torch.empty((gc, wl.n_grid, wl.n_grid), dtype=torch.float32, device=dev)
     compress = COMPRESS[args.workload]
     stream = torch.cuda.current_stream()
     ev_g = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -217,7 +226,7 @@ def run_ours(args, rank, world, local_rank):
         g.zero()
         if k is not None:
             ev_p[k][0].record(stream)
-        wg.vis_compress(g, tab, batch, wlst, compress=compress)
+        wg.vis_compress(g, tab, batch, wlst, compress=compress, interleave=inter)
         if k is not None:
             ev_p[k][1].record(stream)
             ev_g[k][0].record(stream)
@@ -228,7 +237,7 @@ def run_ours(args, rank, world, local_rank):
 
     # one-off, outside the timed region: pick the gridder plan on this batch
     g.zero()
-    wg.vis_compress(g, tab, batch, wlst, compress=compress)
+    wg.vis_compress(g, tab, batch, wlst, compress=compress, interleave=inter)
     plan = wg.grid_autotune(g, tab, wlst, candidates=STEP_PLANS, repeats=2)[:3]
 
     clocks = ClockSampler(local_rank)
@@ -261,7 +270,7 @@ def run_ours(args, rank, world, local_rank):
 
     # precision variants (reduced-precision tables, half visibilities, compensated flushes)
     variants = {}
-    if not args.no_variants:
+    if not args.no_variants and not inter:
         vis_h, scale_h = synth.to_half_vis(wl.vis)
         batch_h = wg.VisBatch(uvw_d, freq_d, vis_h, wl.weight, wl.flag, vis_scale=scale_h)
         for name, store, half, comp in (("fp32+compensated", "f32", False, True), ("f16 table", "f16", False, False),
@@ -345,7 +354,7 @@ def run_ours(args, rank, world, local_rank):
             stream.wait_event(copied[k % 2])
             b = slots[k % 2][1]
             g.zero()
-            wg.vis_compress(g, tab, b, wlst, compress=compress)
+            wg.vis_compress(g, tab, b, wlst, compress=compress, interleave=inter)
             wg.grid_vis(g, tab, wlst)
             wg.grid_correct(g, tab, mode=wg.IMAGE_STOKES_I, out=img)
             consumed[k % 2].record(stream)
@@ -415,7 +424,7 @@ def run_ours(args, rank, world, local_rank):
         nc, nt = CPU_SAMPLE[args.workload]
         procs = min(CPU_PROCS.get(args.workload, 1), os.cpu_count() or 1, nc)
         line["cpu_baseline"] = cpu_sample(args.workload, nc if procs > 1 else min(nc, 4), nt, procs)
-        line["grid_error"] = grid_error_sample(args.workload, dev, plan)
+        line["grid_error"] = grid_error_sample(args.workload, dev, plan, inter)
     return line
 
 
@@ -672,15 +681,20 @@ def _oracle_setup(workload, chans, n_times):
 
 
 def _oracle_run(workload, wl, ot):
-    """The FP64 oracle (placement, compression, gridding) on one channel; returns (total updates,
-    start, end) on the host's monotonic clock."""
+    """The FP64 oracle (placement, compression, gridding) on a workload slice; returns (total
+    updates, start, end) on the host's monotonic clock."""
     import numpy as np
 
     import oracle
+    from oracle.grid import compress
     vis, w, f = wl.vis.numpy(), wl.weight.numpy(), wl.flag.numpy()
+    inter = INTERLEAVE.get(workload, False)
     t0 = time.perf_counter()
     pl = oracle.place(wl.uvw, wl.freq, wl.du, wl.n_grid, ot, flag=f)
-    if COMPRESS[workload]:
+    if COMPRESS[workload] and inter:
+        g, c, *_ = compress(pl, vis, w, f, interleave=True)
+        oracle.grid_compressed(pl, ot, vis, w, f, wl.n_grid, interleave=True)
+    elif COMPRESS[workload]:
         g, c = oracle.classify(pl)
         oracle.grid_compressed(pl, ot, vis, w, f, wl.n_grid)
     else:
@@ -708,6 +722,17 @@ def cpu_sample(workload, n_chan, n_times, procs=1):
     procs > 1 spreads the channels over worker processes (spawned, so no CUDA state is
     inherited) that start their timed sections together; the all-core rate is all updates over
     the span of the timed sections, the single-core rate the mean over channels."""
+    if procs <= 1 and INTERLEAVE.get(workload, False):
+        import oracle
+        import synth
+        wl = synth.make(workload, n_chan=n_chan, n_times=n_times)
+        ot = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+        upd, t0, t1 = _oracle_run(workload, wl, ot)
+        return {"value": round(upd / (t1 - t0) / 1e9, 4), "unit": "G grid-point updates/s (total rate)",
+                "cores": 1, "kind": "oracle", "seconds": round(t1 - t0, 2),
+                "sample": "%s geometry, %d interleaved channels x %d time steps x %d baselines (%d records), FP64 "
+                          "oracle: placement + compression + gridding onto one grid, single thread" % (
+                              workload, n_chan, n_times, wl.n_baselines, wl.rows * wl.n_chan)}
     if procs <= 1:
         sets, ot = _oracle_setup(workload, range(n_chan), n_times)
         res = [_oracle_run(workload, wl, ot) for wl in sets]
@@ -739,7 +764,7 @@ def cpu_sample(workload, n_chan, n_times, procs=1):
                           workload, n_chan, n_times, res[0][3], sum(r[4] for r in res), procs)}
 
 
-def grid_error_sample(workload, dev, plan):
+def grid_error_sample(workload, dev, plan, interleave=False):
     """Grid error of the CUDA path against the FP64 oracle (plain definition, eq. "gridding") on a
     seeded slice of the workload (300 baselines x 24 steps x 2 channels), with the bench's plan."""
     import numpy as np
@@ -750,18 +775,18 @@ def grid_error_sample(workload, dev, plan):
     import synth
     wl = synth.make(workload, n_chan=2, n_times=24, n_baselines=300)
     tab = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
-    g = wg.Grid(wl.n_grid, wl.du, wl.n_pol, wl.n_chan, device=dev)
+    g = wg.Grid(wl.n_grid, wl.du, wl.n_pol, 1 if interleave else wl.n_chan, device=dev)
     b = wg.VisBatch(torch.as_tensor(wl.uvw, device=dev), torch.as_tensor(wl.freq, device=dev), wl.vis.to(dev),
                     wl.weight.to(dev), wl.flag.to(dev))
     w = wg.WorkList(wl.rows * wl.n_chan, wl.n_chan, wl.n_pol)
-    wg.vis_compress(g, tab, b, w, compress=COMPRESS[workload])
+    wg.vis_compress(g, tab, b, w, compress=COMPRESS[workload], interleave=interleave)
     w.plan(tab, *plan)
     wg.grid_vis(g, tab, w)
     got = g.data.cpu().numpy()
     ot = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
     f = wl.flag.numpy()
     pl = oracle.place(wl.uvw, wl.freq, wl.du, wl.n_grid, ot, flag=f)
-    ref = oracle.grid_plain(pl, ot, wl.vis.numpy(), wl.weight.numpy(), f, wl.n_grid)
+    ref = oracle.grid_plain(pl, ot, wl.vis.numpy(), wl.weight.numpy(), f, wl.n_grid, interleave=interleave)
     return {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
             "max_abs_over_max": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
             "reference": "FP64 oracle, plain gridding definition",

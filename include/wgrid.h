@@ -76,6 +76,11 @@ extern "C" {
                              /* griddable records are unchanged (all-flagged ones stay   */
                              /* excluded): gridding is then the adjoint of PREDICT-mode  */
                              /* degridding                                               */
+#define WG_PREP_INTERLEAVE 4 /* channel interleaving (Sec. 5.4, batch 1): the records of */
+                             /* all channels, in natural order row * n_chan + chan, grid */
+                             /* onto a one-channel grid (multi-frequency synthesis), and */
+                             /* a record compresses into the previous record in that     */
+                             /* order; the work list is created with the vis channels    */
 
 /* grid_correct modes */
 #define WG_IMAGE_PER_POL 0 /* output float [n_chan][n_pol][N][N]                      */
@@ -219,15 +224,19 @@ typedef struct wg_stats {
  *      footprint origin (x - (S_k-1)/2, y - (S_k-1)/2); kernel pointer
  *      z = offset_k + ((frac_v - lo) beta + (frac_u - lo)) S_k^2, lo = -((beta-1)/2)
  *      griddable: k <= K-1, footprint inside the grid, some polarisation unflagged;
- *   A2 compression (if flags & WG_PREP_COMPRESS): record (r, c) is compressed into (r-1, c) when
- *      both are griddable with equal footprint origin and z (eq. "ci");
- *   A3 compaction of gridded records into channel-major lists, segmented into tasks;
+ *   A2 compression (if flags & WG_PREP_COMPRESS): record (r, c) is compressed into (r-1, c)
+ *      (with WG_PREP_INTERLEAVE: into the previous record r * n_chan + c - 1) when both are
+ *      griddable with equal footprint origin and z (eq. "ci");
+ *   A3 compaction of gridded records into channel-major lists (interleaved: one list in record
+ *      order), segmented into tasks;
  *   A4 gamma = sum over each run of eps (1-f) psi-conj(vis) (eqs. "compress1",
  *      "conjugatetake"), FP32 (eps (1-f) = 1 with WG_PREP_UNWEIGHTED);
  *   A5 the normaliser terms (eps (1-f) zeta, summed per run) and statistics, added into the
  *      grid's N_p and counters when grid_vis runs.
  * `grid` supplies N and du; `table` the planes, supports and zeta.  The work list keeps
  * the results until the next call on it.
+ * With WG_PREP_INTERLEAVE the grid must have one channel (SHAPE otherwise) and the work list's
+ * runs hold record indices instead of rows.
  * Errors: INVALID_ARG, SHAPE (n_chan/n_pol/du mismatch), CAPACITY (also when n_chan x
  * (16 n_pol + 1) bytes exceed the 227 KB preparation tile, e.g. more than 3575 channels at
  * n_pol = 4), CUDA. */
@@ -239,7 +248,8 @@ int worklist_stats(const wg_worklist* wl, wg_stats* out, void* stream);
 
 /* Device views of the work list, for inspection and tests.  entries: int32 [n][4] with
  * {x0 | y0 << 16, (-x0 mod S) | (-y0 mod S) << 16, z, k | chan << 16}; gamma: complex64
- * [n][n_pol]; runs: int32 [n][2] first and last row of each gridded run; rec_class: uint8
+ * [n][n_pol]; runs: int32 [n][2] first and last row of each gridded run (first and last
+ * record when interleaved); rec_class: uint8
  * per input record, bit0 = g, bit1 = c, bit2 = griddable, bit3 = take-conjugate (w' < 0).  *n_entries is read from the
  * device (synchronises `stream`). */
 int worklist_view(const wg_worklist* wl, const int32_t** entries, const void** gamma,

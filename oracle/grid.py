@@ -5,6 +5,11 @@ compress         : the compression of Sec. 4.3.3 with eqs. "compress1"/"conjugat
                    (sequential loop in oracle.c).
 grid_compressed  : grids the compressed list; equals grid_plain up to rounding.
 normaliser       : eq. "normalizer" (Sec. 4.3.2), N_p per channel.
+
+interleave=True is channel interleaving (Sec. 5.4, batch 1: the channels of a record row are
+interleaved and all records gridded onto one grid, as in multi-frequency synthesis): the grid
+has one channel, a record's predecessor for compression is the previous record in natural
+order row*C + chan, and N_p sums over all records.
 stats            : the four statistics of Sec. 4.3.4.
 degrid           : adjoint of the gridding map.  The vis -> grid map is only R-linear
                    (psi = -1 records are conjugated), so its adjoint under Re<a,b> is
@@ -39,15 +44,21 @@ def _grid_records(sel, chan, x0, y0, z, S, q, P, N, C, table):
     return grid
 
 
-def grid_plain(pl, table, vis, weight, flag, n_grid):
+def _grid_chan(pl, interleave):
+    """(grid channel of every record, number of grid channels)."""
+    return (np.zeros_like(pl.chan), 1) if interleave else (pl.chan, pl.C)
+
+
+def grid_plain(pl, table, vis, weight, flag, n_grid, interleave=False):
     """grid[c][y][x][p] = sum over griddable records of q_{i,p} * K_i (eq. "gridding")."""
     P = np.asarray(vis).shape[-1]
     q = weighted_vis(pl, vis, weight, flag)
     sel = pl.griddable
-    return _grid_records(sel, pl.chan, pl.x0, pl.y0, pl.z, pl.S, q[sel], P, n_grid, pl.C, table)
+    chan, C = _grid_chan(pl, interleave)
+    return _grid_records(sel, chan, pl.x0, pl.y0, pl.z, pl.S, q[sel], P, n_grid, C, table)
 
 
-def compress(pl, vis, weight, flag):
+def compress(pl, vis, weight, flag, interleave=False):
     """Returns (g, c, list_rec, list_last, gamma) following the sequential compression."""
     rows, C = pl.rows, pl.C
     P = np.asarray(vis).shape[-1]
@@ -66,26 +77,29 @@ def compress(pl, vis, weight, flag):
     lrec = np.zeros(n, np.int64)
     llast = np.zeros(n, np.int64)
     gamma = np.zeros((n, P), np.complex128)
-    ne = lib.or_compress(rows, C, P, _p(gd), _p(x0), _p(y0), _p(z), _p(psi), _p(v), _p(w), _p(f),
+    ne = lib.or_compress(rows, C, P, 1 if interleave else 0, _p(gd), _p(x0), _p(y0), _p(z), _p(psi), _p(v), _p(w), _p(f),
                          _p(g), _p(c), _p(head), _p(lrec), _p(llast), _p(gamma))
     return (g.astype(bool), c.astype(bool), lrec[:ne].copy(), llast[:ne].copy(), gamma[:ne].copy())
 
 
-def grid_compressed(pl, table, vis, weight, flag, n_grid):
+def grid_compressed(pl, table, vis, weight, flag, n_grid, interleave=False):
     P = np.asarray(vis).shape[-1]
-    g, c, lrec, llast, gamma = compress(pl, vis, weight, flag)
-    return _grid_records(lrec, pl.chan, pl.x0, pl.y0, pl.z, pl.S, gamma, P, n_grid, pl.C, table)
+    g, c, lrec, llast, gamma = compress(pl, vis, weight, flag, interleave)
+    chan, C = _grid_chan(pl, interleave)
+    return _grid_records(lrec, chan, pl.x0, pl.y0, pl.z, pl.S, gamma, P, n_grid, C, table)
 
 
-def normaliser(pl, table, weight, flag) -> np.ndarray:
-    """N[c][p] = sum_i eps (g+c)(1-f) zeta_i  (eq. "normalizer"); (g+c) = griddable."""
+def normaliser(pl, table, weight, flag, interleave=False) -> np.ndarray:
+    """N[c][p] = sum_i eps (g+c)(1-f) zeta_i  (eq. "normalizer"); (g+c) = griddable.
+    Interleaved: one row, the sum over all records."""
     rows, C = pl.rows, pl.C
     P = np.asarray(weight).shape[-1]
     wf = np.asarray(weight, np.float64).reshape(-1, P) * (1.0 - np.asarray(flag, np.float64).reshape(-1, P))
     zeta = np.where(pl.griddable, table.zeta[np.maximum(pl.zeta_idx, 0)], 0.0)
     contrib = wf * zeta[:, None]
+    chan, C = _grid_chan(pl, interleave)
     out = np.zeros((C, P))
-    np.add.at(out, pl.chan, contrib)
+    np.add.at(out, chan, contrib)
     return out
 
 
@@ -97,14 +111,15 @@ def stats(pl, g, c):
             "updates": int((S2 * g).sum()), "updates_saved": int((S2 * c).sum())}
 
 
-def degrid(pl, table, grid, weight=None, flag=None, adjoint=False) -> np.ndarray:
+def degrid(pl, table, grid, weight=None, flag=None, adjoint=False, interleave=False) -> np.ndarray:
     """Per record: m_p = sum_ij conj(K) grid_p over the footprint, conjugated back where
     psi = -1.  adjoint=True also applies eps (1 - f), giving the exact adjoint of the
     vis -> grid map.  Non-griddable records get 0.  Returns complex128 [rows*C, P]."""
     C, N, _, P = grid.shape
     sel = np.nonzero(pl.griddable)[0]
+    chan, _ = _grid_chan(pl, interleave)
     a = [np.ascontiguousarray(v[sel], dtype=t) for v, t in
-         ((pl.chan, np.int32), (pl.x0, np.int32), (pl.y0, np.int32), (pl.z, np.int64), (pl.S, np.int32))]
+         ((chan, np.int32), (pl.x0, np.int32), (pl.y0, np.int32), (pl.z, np.int64), (pl.S, np.int32))]
     m = np.zeros((sel.shape[0], P), np.complex128)
     g = np.ascontiguousarray(grid, dtype=np.complex128)
     tab = np.ascontiguousarray(table.data, dtype=np.complex128)

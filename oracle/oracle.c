@@ -74,9 +74,11 @@ void or_degrid(int64_t n, const int32_t* chan, const int32_t* x0, const int32_t*
  * Compression (Sec. 4.3.3 "Compression", eq. "ci"; Algorithms "compressindex" and the
  * "Compress and Weigh Visibilities" operator, eqs. "compress1"/"conjugatetake").
  *
- * Records are visited per channel in row order (row = baseline-major, time-minor).
- * Record i is compressed into its predecessor i-1 (same channel, previous row) when
- * both are griddable and they share the footprint origin (x0,y0) and the kernel
+ * Records are visited per channel in row order (row = baseline-major, time-minor), or,
+ * with channel interleaving (the thesis's multi-frequency synthesis onto one grid, Sec. 5.4
+ * batch 1), as one sequence in natural record order i = row*C + chan.  Record i is
+ * compressed into its predecessor (same channel, previous row; interleaved: record i-1)
+ * when both are griddable and they share the footprint origin (x0,y0) and the kernel
  * pointer z.  A record that is griddable and not compressed starts a new gridded
  * entry.  For each gridded entry the weighted, flagged, psi-conjugated visibilities
  * of the whole run are summed.
@@ -87,26 +89,29 @@ void or_degrid(int64_t n, const int32_t* chan, const int32_t* x0, const int32_t*
  *   list_rec[e]         record index of entry e (the "Gridding Index" g^d)
  *   list_last[e]        last record of the run (the "Last Compressed Entry Index")
  *   gamma[e][P][2]      summed visibilities
- * Entries are ordered channel-major, then row.  Returns the number of entries.
+ * Entries are ordered channel-major, then row (interleaved: by record).  Returns the number
+ * of entries.
  */
-int64_t or_compress(int64_t rows, int32_t C, int32_t P, const uint8_t* griddable,
+int64_t or_compress(int64_t rows, int32_t C, int32_t P, int32_t interleave, const uint8_t* griddable,
                     const int32_t* x0, const int32_t* y0, const int64_t* z, const int8_t* psi,
                     const float* vis /* [rows][C][P][2] */, const float* weight, const uint8_t* flag,
                     uint8_t* g, uint8_t* c, int64_t* head_of, int64_t* list_rec, int64_t* list_last,
                     double* gamma)
 {
     int64_t ne = 0;
-    for (int32_t ch = 0; ch < C; ++ch) {
+    const int32_t n_seq = interleave ? 1 : C;              /* sequences: channels, or one */
+    const int64_t len = interleave ? rows * C : rows;       /* records per sequence */
+    for (int32_t ch = 0; ch < n_seq; ++ch) {
         int64_t cur = -1;
-        for (int64_t row = 0; row < rows; ++row) {
-            const int64_t i = row * C + ch;
+        for (int64_t s = 0; s < len; ++s) {
+            const int64_t i = interleave ? s : s * C + ch;
+            const int64_t ip = interleave ? i - 1 : i - C;  /* predecessor in the sequence */
             g[i] = 0;
             c[i] = 0;
             head_of[i] = -1;
             if (!griddable[i]) { cur = -1; continue; }
-            const int64_t ip = i - C;
             int comp = 0;
-            if (row > 0 && griddable[ip] && x0[i] == x0[ip] && y0[i] == y0[ip] && z[i] == z[ip])
+            if (s > 0 && griddable[ip] && x0[i] == x0[ip] && y0[i] == y0[ip] && z[i] == z[ip])
                 comp = 1;
             if (comp) {
                 c[i] = 1;

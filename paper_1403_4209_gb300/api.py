@@ -24,6 +24,7 @@ IMAGE_PER_POL_RAW = CONST["WG_IMAGE_PER_POL_RAW"]
 IMAGE_TRANSPOSE = CONST["WG_IMAGE_TRANSPOSE"]
 PREP_COMPRESS = CONST["WG_PREP_COMPRESS"]
 PREP_UNWEIGHTED = CONST["WG_PREP_UNWEIGHTED"]
+PREP_INTERLEAVE = CONST["WG_PREP_INTERLEAVE"]
 
 
 def _stream(stream=None):
@@ -259,8 +260,11 @@ class WorkList:
 
 
 def vis_compress(grid: Grid, table: ConvTable, batch: VisBatch, worklist: WorkList, compress: bool = True,
-                 unweighted: bool = False, stream=None):
-    flags = (PREP_COMPRESS if compress else 0) | (PREP_UNWEIGHTED if unweighted else 0)
+                 unweighted: bool = False, interleave: bool = False, stream=None):
+    """Preparation phase.  interleave: all channels of the batch grid onto the one-channel
+    `grid` in natural record order, compressing across channels (WG_PREP_INTERLEAVE)."""
+    flags = ((PREP_COMPRESS if compress else 0) | (PREP_UNWEIGHTED if unweighted else 0)
+             | (PREP_INTERLEAVE if interleave else 0))
     check(lib.vis_compress(grid.handle, table.handle, ctypes.byref(batch.struct), flags,
                            worklist.handle, _stream(stream)), "vis_compress")
 

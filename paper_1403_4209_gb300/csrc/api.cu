@@ -305,11 +305,14 @@ int worklist_create(int64_t max_records, int32_t C, int32_t P, wg_worklist** out
     return WG_OK;
 }
 
-static int check_vis(const Grid& g, const Table& t, const wg_vis_in* in)
+static int check_vis(const Grid& g, const Table& t, const wg_vis_in* in, bool interleave)
 {
     if (!in) return fail(WG_E_INVALID_ARG, "null vis input");
     if (in->n_rows < 0) return fail(WG_E_INVALID_ARG, "n_rows must be >= 0");
-    if (in->n_chan != g.n_chan || in->n_pol != g.n_pol)
+    if (interleave && (g.n_chan != 1 || in->n_pol != g.n_pol || in->n_chan < 1))
+        return fail(WG_E_SHAPE, "interleaved channels need a one-channel grid with the vis polarisations "
+                                "(grid: %d channels, %d pols; vis: %d pols)", g.n_chan, g.n_pol, in->n_pol);
+    if (!interleave && (in->n_chan != g.n_chan || in->n_pol != g.n_pol))
         return fail(WG_E_SHAPE, "vis shape (chan %d, pol %d) differs from the grid's (%d, %d)", in->n_chan, in->n_pol, g.n_chan, g.n_pol);
     if (in->n_rows > 0 && (!in->uvw || !in->freq_hz || !in->vis || !in->weight || !in->flag))
         return fail(WG_E_INVALID_ARG, "null input array");
@@ -329,13 +332,14 @@ int vis_compress(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, int
 {
     t_err[0] = 0;
     if (!gh || !th || !wh) return fail(WG_E_INVALID_ARG, "vis_compress: null handle");
-    int rc = check_vis(gh->g, th->t, in);
+    int rc = check_vis(gh->g, th->t, in, (flags & WG_PREP_INTERLEAVE) != 0);
     if (rc != WG_OK) return rc;
     WorkList& w = wh->w;
     if (in->n_chan != w.C || in->n_pol != w.P) return fail(WG_E_SHAPE, "work list was created for %d channels, %d pols", w.C, w.P);
     if (in->n_rows * (int64_t)in->n_chan > w.cap)
         return fail(WG_E_CAPACITY, "%lld records exceed the work list capacity %lld", (long long)(in->n_rows * (int64_t)in->n_chan), (long long)w.cap);
-    if (flags & ~(WG_PREP_COMPRESS | WG_PREP_UNWEIGHTED)) return fail(WG_E_INVALID_ARG, "unknown vis_compress flags %d", flags);
+    if (flags & ~(WG_PREP_COMPRESS | WG_PREP_UNWEIGHTED | WG_PREP_INTERLEAVE))
+        return fail(WG_E_INVALID_ARG, "unknown vis_compress flags %d", flags);
     return launch_prep(th->t, gh->g, *in, flags, w, S(stream));
 }
 
@@ -383,7 +387,8 @@ int grid_vis(wg_grid* gh, const wg_table* th, const wg_worklist* wh, void* strea
     if (!gh || !th || !wh) return fail(WG_E_INVALID_ARG, "grid_vis: null handle");
     Grid& g = gh->g;
     const WorkList& w = wh->w;
-    if (w.C != g.n_chan || w.P != g.n_pol) return fail(WG_E_SHAPE, "work list shape differs from the grid's");
+    if ((w.interleave ? 1 : w.C) != g.n_chan || w.P != g.n_pol)
+        return fail(WG_E_SHAPE, "work list shape differs from the grid's");
     if (w.N != 0 && w.N != g.n) return fail(WG_E_SHAPE, "work list was prepared for N=%d, grid has N=%d", w.N, g.n);
     return launch_grid(g, th->t, w, S(stream));
 }
@@ -490,9 +495,9 @@ int degrid_vis(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, const
     t_err[0] = 0;
     if (!gh || !th || !wh || !vis_out) return fail(WG_E_INVALID_ARG, "degrid_vis: null argument");
     if (mode != WG_DEGRID_PREDICT && mode != WG_DEGRID_ADJOINT) return fail(WG_E_INVALID_ARG, "unknown degrid mode %d", mode);
-    int rc = check_vis(gh->g, th->t, in);
-    if (rc != WG_OK) return rc;
     const WorkList& w = wh->w;
+    int rc = check_vis(gh->g, th->t, in, w.interleave);
+    if (rc != WG_OK) return rc;
     if (w.rows != in->n_rows || w.C != in->n_chan) return fail(WG_E_SHAPE, "work list was prepared for a different batch");
     if (reinterpret_cast<uintptr_t>(vis_out) & 7) return fail(WG_E_INVALID_ARG, "vis_out must be 8-byte aligned");
     return launch_degrid(gh->g, th->t, *in, w, mode, static_cast<float2*>(vis_out), S(stream));

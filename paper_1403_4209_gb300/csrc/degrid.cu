@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256, 4) k_degrid(const int4* __restrict__ entr
                                                 int N, int C, const double* __restrict__ uvw,
                                                 const float* __restrict__ weight, const uint8_t* __restrict__ flag,
                                                 int adjoint, float2* __restrict__ out, int K, int64_t n_samples,
-                                                int64_t rows, unsigned int* __restrict__ counter,
+                                                int64_t rows, int interleave, unsigned int* __restrict__ counter,
                                                 long long* __restrict__ dropped)
 {
     const long long n = scal[0];
@@ -86,11 +86,11 @@ __global__ void __launch_bounds__(256, 4) k_degrid(const int4* __restrict__ entr
             const int x0 = E.x & 0xFFFF, y0 = (E.x >> 16) & 0xFFFF, z = E.z;
             const int2 run = runs[e];
             if (x0 + S > N || y0 + S > N || z < 0 || (int64_t)z + (int64_t)S * S > n_samples || run.x < 0 ||
-                run.y < run.x || (int64_t)run.y >= rows) {
+                run.y < run.x || (int64_t)run.y >= (interleave ? rows * C : rows)) {
                 if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
                 continue;
             }
-            const float2* gch = grid + (size_t)ch * N * N * P;
+            const float2* gch = grid + (size_t)ch * N * N * P;   // channel 0 when interleaved
             f32x2 A[P], B[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) A[p] = B[p] = 0ull;
@@ -125,9 +125,11 @@ __global__ void __launch_bounds__(256, 4) k_degrid(const int4* __restrict__ entr
                     acc[p].y += __shfl_xor_sync(0xffffffffu, acc[p].y, o);
                 }
             }
-            for (int row = run.x + lane; row <= run.y; row += 32) {
-                const int64_t rec = (int64_t)row * C + ch;
-                const bool neg = uvw[3 * (int64_t)row + 2] < 0.0;
+            // the run's records: rows run.x..run.y of channel ch, or records run.x..run.y
+            for (int r = run.x + lane; r <= run.y; r += 32) {
+                const int64_t rec = interleave ? (int64_t)r : (int64_t)r * C + ch;
+                const int64_t row = interleave ? (int64_t)r / C : (int64_t)r;
+                const bool neg = uvw[3 * row + 2] < 0.0;
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     float2 v = neg ? make_float2(acc[p].x, -acc[p].y) : acc[p];
@@ -157,7 +159,8 @@ static int degrid_impl(const Grid& g, const Table& t, const wg_vis_in& in, const
     const int blocks = num_sms() * blocks_per_sm;
     k_degrid<P><<<blocks, 256, 0, s>>>(wl.entries, wl.runs, wl.scal, t.supports_d, t.data, g.data, g.n, in.n_chan,
                                        in.uvw, in.weight, in.flag, mode == WG_DEGRID_ADJOINT ? 1 : 0, out, t.K,
-                                       t.n_samples, in.n_rows, wl.task_counter + 1, wl.scal + 3);
+                                       t.n_samples, in.n_rows, wl.interleave ? 1 : 0, wl.task_counter + 1,
+                                       wl.scal + 3);
     WG_LAUNCHED("k_degrid");
     return WG_OK;
 }

@@ -81,6 +81,8 @@ extern "C" int grid_vis_noalloc(const wg_grid_view* view, const wg_table* th, co
     if (reinterpret_cast<uintptr_t>(view->data) & 15) return fail(WG_E_INVALID_ARG, "grid buffer must be 16-byte aligned");
     if (in->n_chan != view->n_chan || in->n_pol != view->n_pol) return fail(WG_E_SHAPE, "vis shape differs from the grid's");
     if (in->n_rows < 0) return fail(WG_E_INVALID_ARG, "n_rows must be >= 0");
+    if (compress != 0 && compress != WG_PREP_COMPRESS)
+        return fail(WG_E_INVALID_ARG, "compress must be 0 or WG_PREP_COMPRESS (got %d)", compress);
     if (in->n_rows > 0 && (!in->uvw || !in->freq_hz || !in->vis || !in->weight || !in->flag))
         return fail(WG_E_INVALID_ARG, "null input array");
     if (reinterpret_cast<uintptr_t>(in->vis) & 7) return fail(WG_E_INVALID_ARG, "vis must be 8-byte aligned");

@@ -19,6 +19,7 @@
 //               per block of `slots` footprint points of its largest support.  The plan can be
 //               redone with other parameters (launch_plan) without repeating the preparation.
 #include <cstdio>
+#include <type_traits>
 
 #include <cuda_fp16.h>
 
@@ -234,7 +235,7 @@ __global__ void k_chan_scale(const double* __restrict__ freq, int C, double beta
 }
 
 template <int P>
-__global__ void __launch_bounds__(512) k_classify(const double* __restrict__ uvw, const double* __restrict__ lam_inv,
+__global__ void __launch_bounds__(512, 3) k_classify(const double* __restrict__ uvw, const double* __restrict__ lam_inv,
                                                   const double* __restrict__ sc, const float* __restrict__ lam_f,
                                                   const float* __restrict__ sc_f, const uint8_t* __restrict__ flag,
                                                   int64_t rows, int rpb, PlaceParams pp, int4* __restrict__ rinfo,
@@ -278,16 +279,24 @@ __global__ void __launch_bounds__(512) k_classify(const double* __restrict__ uvw
         const int4 info = s_info[j];
         const int gd = (info.w >> kBitGd) & 1;
         int c = 0;
-        if (pp.compress && gd && row > 0) {
+        // the predecessor: the previous row of the channel, or with interleaving the previous
+        // record in natural order (the last channel of the previous row for channel 0)
+        if (pp.compress && gd && (pp.interleave ? rec > 0 : row > 0)) {
             int4 pinfo;
-            if (rr > 0) pinfo = s_info[j - C];
-            else pinfo = place(uvw, row - 1, s_row[0], lam_inv[ch], sc[ch], lam_f[ch], sc_f[ch], flag, rec - C, P,
-                               pp).info;
+            if (!pp.interleave && rr > 0) {
+                pinfo = s_info[j - C];
+            } else if (pp.interleave && j > 0) {
+                pinfo = s_info[j - 1];
+            } else {
+                const int pc = pp.interleave ? C - 1 : ch;
+                pinfo = place(uvw, row - 1, s_row[0], lam_inv[pc], sc[pc], lam_f[pc], sc_f[pc], flag,
+                              (row - 1) * C + pc, P, pp).info;
+            }
             c = ((pinfo.w >> kBitGd) & 1) && pinfo.x == info.x && pinfo.z == info.z;
         }
         const int g = gd & (c ^ 1);
         s_gc[j] = (unsigned char)(g | (c << 1) | (gd << 2) | (((info.w >> kBitNeg) & 1) << 3));
-        s_scan[ch * nrows + rr] = g;
+        s_scan[pp.interleave ? j : ch * nrows + rr] = g;
         if (gd) {
             const unsigned long long S = (unsigned long long)__ldg(&pp.supports[info.w & 0xFFF]);
             n_gd += 1;
@@ -309,7 +318,7 @@ __global__ void __launch_bounds__(512) k_classify(const double* __restrict__ uvw
     }
     __syncthreads();
 
-    // pass 3: channel-major exclusive scan of g -> rank inside the tile
+    // pass 3: channel-major (interleaved: natural-order) exclusive scan of g -> rank in the tile
     block_exclusive_scan(s_scan, nrec, warp_tot);
 
     // pass 4: outputs
@@ -318,13 +327,14 @@ __global__ void __launch_bounds__(512) k_classify(const double* __restrict__ uvw
         const int64_t rec = (row0 + rr) * C + ch;
         int4 info = s_info[j];
         const int gc = s_gc[j];
-        const int rank = s_scan[ch * nrows + rr] - s_scan[ch * nrows];
+        const int rank = pp.interleave ? s_scan[j] - s_scan[0] : s_scan[ch * nrows + rr] - s_scan[ch * nrows];
         info.w |= ((gc & 1) << kBitG) | (((gc >> 1) & 1) << kBitC) | (rank << 16);
         rinfo[rec] = info;
         rclass[rec] = (uint8_t)gc;
     }
-    for (int ch = threadIdx.x; ch < C; ch += blockDim.x)
-        tile_cnt[tile * C + ch] = s_scan[(ch + 1) * nrows] - s_scan[ch * nrows];
+    for (int ch = threadIdx.x; ch < C; ch += blockDim.x)   // interleaved: one list, channel 0's
+        tile_cnt[tile * C + ch] = pp.interleave ? (ch == 0 ? s_scan[nrec] - s_scan[0] : 0)
+                                                : s_scan[(ch + 1) * nrows] - s_scan[ch * nrows];
     const int slot = (int)(tile % kNormSlots);
     if (threadIdx.x == 0) s_stat[ST_RECORDS] = (unsigned long long)nrec;
     __syncthreads();
@@ -465,7 +475,7 @@ __device__ __forceinline__ void weighted_vec(const __half2* __restrict__ vis, co
 // memory when the run crosses the tile's end; it writes its entry, gamma and run, and adds
 // zeta(sub-kernel) x sum eps (1-f) to the normaliser (all records of a run share the
 // sub-kernel).
-template <int P, typename VT>
+template <int P, typename VT, bool IL>
 __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo, const uint8_t* __restrict__ rclass,
                                                  const VT* __restrict__ vis, const float* __restrict__ vis_scale,
                                                  const float* __restrict__ weight, const uint8_t* __restrict__ flag,
@@ -525,9 +535,10 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
         const int j = s_heads[h];
         const int rr = j / C, ch = j - rr * C;
         const int64_t row = row0 + rr, rec = row * C + ch;
+        const int gch = IL ? 0 : ch;       // the grid channel and work-list list
         const int4 info = rinfo[rec];
         const int rank = (info.w >> 16) & 0xFFFF;
-        const int dst = chan_base[ch] + tile_off[tile * C + ch] + rank;
+        const int dst = chan_base[gch] + tile_off[tile * C + gch] + rank;
         if (dst < 0 || (int64_t)dst >= cap_entries) {   // cannot happen with a consistent scan
             atomicAdd(reinterpret_cast<unsigned long long*>(&scal[3]), 1ull);
             continue;
@@ -539,48 +550,88 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
             acc[p] = s_q[(size_t)p * cap + j];
             wsum[p] = s_w[(size_t)p * cap + j];
         }
-        int64_t last = row;
-        int r2 = rr + 1;
-        for (; r2 < nrows; ++r2) {
-            const int j2 = r2 * C + ch;
-            if (!(s_cls[j2] & 2)) break;
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const float2 q = s_q[(size_t)p * cap + j2];
-                acc[p].x += q.x;
-                acc[p].y += q.y;
-                wsum[p] += s_w[(size_t)p * cap + j2];
-            }
-            last = row0 + r2;
-        }
-        if (r2 == nrows) {                              // the run may go on in the next tiles
-            const float scale = vis_scale ? vis_scale[ch] : 1.0f;
-            for (int64_t g2 = row0 + nrows; g2 < rows; ++g2) {
-                const int64_t rc2 = g2 * C + ch;
-                const int cls2 = rclass[rc2];
-                if (!(cls2 & 2)) break;
+        // the run: the successors (next rows of the channel; interleaved: next records) while
+        // they are compressed, first in this tile, then in the next tiles.  `last` is the run's
+        // last row (interleaved: last record).  The two orders keep separate loops.
+        int64_t last;
+        if constexpr (!IL) {
+            last = row;
+            int r2 = rr + 1;
+            for (; r2 < nrows; ++r2) {
+                const int j2 = r2 * C + ch;
+                if (!(s_cls[j2] & 2)) break;
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    float wf;
-                    const float2 q = weighted(vis, weight, flag, rc2 * P + p, scale, (cls2 >> 3) & 1, unweighted, wf);
+                    const float2 q = s_q[(size_t)p * cap + j2];
                     acc[p].x += q.x;
                     acc[p].y += q.y;
-                    wsum[p] += wf;
+                    wsum[p] += s_w[(size_t)p * cap + j2];
                 }
-                last = g2;
+                last = row0 + r2;
+            }
+            if (r2 == nrows) {
+                const float scale = vis_scale ? vis_scale[ch] : 1.0f;
+                for (int64_t g2 = row0 + nrows; g2 < rows; ++g2) {
+                    const int64_t rc2 = g2 * C + ch;
+                    const int cls2 = rclass[rc2];
+                    if (!(cls2 & 2)) break;
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        float wf;
+                        const float2 q = weighted(vis, weight, flag, rc2 * P + p, scale, (cls2 >> 3) & 1, unweighted, wf);
+                        acc[p].x += q.x;
+                        acc[p].y += q.y;
+                        wsum[p] += wf;
+                    }
+                    last = g2;
+                }
+            }
+        } else {
+            last = rec;
+            int j2 = j + 1;
+            for (; j2 < nrec; ++j2) {
+                if (!(s_cls[j2] & 2)) break;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const float2 q = s_q[(size_t)p * cap + j2];
+                    acc[p].x += q.x;
+                    acc[p].y += q.y;
+                    wsum[p] += s_w[(size_t)p * cap + j2];
+                }
+                last = row0 * C + j2;
+            }
+            if (j2 == nrec) {
+                int c2 = 0;                                // channel of the record rc2
+                const int64_t n_all = rows * C;
+                for (int64_t rc2 = (row0 + nrows) * C; rc2 < n_all; ++rc2) {
+                    const int cls2 = rclass[rc2];
+                    if (!(cls2 & 2)) break;
+                    const float scale = vis_scale ? vis_scale[c2] : 1.0f;
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        float wf;
+                        const float2 q = weighted(vis, weight, flag, rc2 * P + p, scale, (cls2 >> 3) & 1, unweighted, wf);
+                        acc[p].x += q.x;
+                        acc[p].y += q.y;
+                        wsum[p] += wf;
+                    }
+                    last = rc2;
+                    c2 = (c2 + 1 == C) ? 0 : c2 + 1;
+                }
             }
         }
         const int k = info.w & 0xFFF;
-        entries[dst] = make_int4(info.x, info.y, info.z, k | (ch << 16));
+        entries[dst] = make_int4(info.x, info.y, info.z, k | (gch << 16));
 #pragma unroll
         for (int p = 0; p < P; ++p) gamma[(int64_t)dst * P + p] = acc[p];
-        runs[dst] = make_int2((int)row, (int)last);
+        // runs: first and last row of the channel, or first and last record when interleaved
+        runs[dst] = make_int2(IL ? (int)rec : (int)row, (int)last);
         const int S = __ldg(&pp.supports[k]);
         const int sub = (info.z - __ldg(&pp.offsets[k])) / (S * S);
         const float zeta = __ldg(&pp.zeta_f[k * pp.beta * pp.beta + sub]);
 #pragma unroll
         for (int p = 0; p < P; ++p)
-            if (wsum[p] != 0.f) atomicAdd(&s_norm[ch * P + p], zeta * wsum[p]);
+            if (wsum[p] != 0.f) atomicAdd(&s_norm[gch * P + p], zeta * wsum[p]);
     }
     __syncthreads();
     const int slot = (int)(tile % kNormSlots);
@@ -690,6 +741,8 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
     pp.lo = -((t.beta - 1) / 2);
     pp.compress = (flags & WG_PREP_COMPRESS) ? 1 : 0;
     pp.unweighted = (flags & WG_PREP_UNWEIGHTED) ? 1 : 0;
+    pp.interleave = (flags & WG_PREP_INTERLEAVE) ? 1 : 0;
+    wl.interleave = pp.interleave != 0;
     pp.C = C;
     pp.P = P;
     pp.w_max = t.w_max;
@@ -734,19 +787,24 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
         const int vec = (va % 16 == 0) && (wa % (4 * P) == 0) && (fa % P == 0);
         if (sm > 227 * 1024)
             return fail(WG_E_CAPACITY, "%d channels x %d polarisations do not fit one preparation tile", C, P);
-        if (in.vis_dtype == WG_VIS_COMPLEX_HALF) {
+        auto launch = [&](auto vt, auto il) -> int {
+            using VT = decltype(vt);
+            constexpr bool IL = decltype(il)::value;
             if (sm > 48 * 1024)
-                WG_CUDA(cudaFuncSetAttribute(k_compact<P, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            k_compact<P, __half2><<<(unsigned)n_tiles, 512, sm, s>>>(
-                wl.rinfo, wl.rclass, reinterpret_cast<const __half2*>(in.vis), in.vis_scale, in.weight, in.flag, rows,
-                rpb, C, wl.tile_cnt, wl.chan_base, pp, wl.entries, wl.gamma, wl.runs, wl.cap, wl.norm_priv, wl.scal, 0);
-        } else {
-            if (sm > 48 * 1024)
-                WG_CUDA(cudaFuncSetAttribute(k_compact<P, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            k_compact<P, float2><<<(unsigned)n_tiles, 512, sm, s>>>(
-                wl.rinfo, wl.rclass, reinterpret_cast<const float2*>(in.vis), nullptr, in.weight, in.flag, rows, rpb,
-                C, wl.tile_cnt, wl.chan_base, pp, wl.entries, wl.gamma, wl.runs, wl.cap, wl.norm_priv, wl.scal, vec);
-        }
+                WG_CUDA(cudaFuncSetAttribute(k_compact<P, VT, IL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_compact<P, VT, IL><<<(unsigned)n_tiles, 512, sm, s>>>(
+                wl.rinfo, wl.rclass, reinterpret_cast<const VT*>(in.vis),
+                std::is_same<VT, float2>::value ? nullptr : in.vis_scale, in.weight, in.flag, rows, rpb,
+                C, wl.tile_cnt, wl.chan_base, pp, wl.entries, wl.gamma, wl.runs, wl.cap, wl.norm_priv, wl.scal,
+                std::is_same<VT, float2>::value ? vec : 0);
+            return WG_OK;
+        };
+        int rc;
+        if (in.vis_dtype == WG_VIS_COMPLEX_HALF)
+            rc = pp.interleave ? launch(__half2{}, std::true_type{}) : launch(__half2{}, std::false_type{});
+        else
+            rc = pp.interleave ? launch(float2{}, std::true_type{}) : launch(float2{}, std::false_type{});
+        if (rc != WG_OK) return rc;
         WG_LAUNCHED("k_compact");
     }
     k_norm_sum<<<1, 256, 0, s>>>(wl.norm_priv, C * P, wl.norm_batch);

@@ -229,12 +229,14 @@ def make(name: str, device: str = "cpu", flag_frac: float = 0.0, n_times: Option
           "degrid_1k"  : 64 stations, 600 steps, 4 channels 120-180 MHz, 4 pols, N=1024, K=16.
           "batch_8k"   : 256 stations log-radial to 10 km, 1800 steps, 64 channels
                          50-350 MHz, 1 pol, N=8192, K=64, supports 9..129.
+          "mfs_2k"     : the wproj_2k geometry with 16 narrow channels (12.2 kHz apart from
+                         150 MHz, a LOFAR subband split 16 ways), for channel interleaving.
     n_times / n_chan / n_baselines shrink a workload to a seeded slice of the same geometry;
     chan0 is the first channel of an n_chan slice.
     chan_group: vis, weight and flag become lists of [rows, chan_group, P] tensors, one per
     group of consecutive channels, each drawn with its own seed (seed + 7919 * group index);
     the (all-ones) weight tensor is shared by the groups."""
-    seeds = {"w0_small": 1000, "wproj_2k": 1001, "degrid_1k": 1002, "batch_8k": 1004}
+    seeds = {"w0_small": 1000, "wproj_2k": 1001, "degrid_1k": 1002, "batch_8k": 1004, "mfs_2k": 1005}
     seed = seeds[name]
     rng = np.random.default_rng(seed)
     if name == "w0_small":
@@ -247,6 +249,12 @@ def make(name: str, device: str = "cpu", flag_frac: float = 0.0, n_times: Option
         enu = stations_gaussian(64, 3000.0, rng)
         T, dt, dec = 3600, 1.0, 45.0
         freq = np.linspace(120e6, 180e6, 16)
+        P, N, K, beta, S_lo, S_hi, taper = 4, 2048, 32, 8, 8, 64, 7
+        noise = 0.01
+    elif name == "mfs_2k":
+        enu = stations_gaussian(64, 3000.0, rng)
+        T, dt, dec = 3600, 1.0, 45.0
+        freq = 150e6 + 195312.5 / 16 * np.arange(16)
         P, N, K, beta, S_lo, S_hi, taper = 4, 2048, 32, 8, 8, 64, 7
         noise = 0.01
     elif name == "degrid_1k":
