@@ -76,6 +76,11 @@ extern "C" {
                              /* griddable records are unchanged (all-flagged ones stay   */
                              /* excluded): gridding is then the adjoint of PREDICT-mode  */
                              /* degridding                                               */
+#define WG_PREP_CROSS_SWAP 8 /* full-Stokes gridding (n_pol = 4): a take-conjugate record */
+                             /* (psi = -1) also swaps its cross hands, pol 1 <-> pol 2,  */
+                             /* since conj(V_XY(u)) = V_YX(-u); the thesis conjugates in */
+                             /* place (eq. "conjugatetake"), exact for the parallel      */
+                             /* hands and U but not for V.  N_p and degridding follow.   */
 #define WG_PREP_INTERLEAVE 4 /* channel interleaving (Sec. 5.4, batch 1): the records of */
                              /* all channels, in natural order row * n_chan + chan, grid */
                              /* onto a one-channel grid (multi-frequency synthesis), and */
@@ -85,6 +90,13 @@ extern "C" {
 /* grid_correct modes */
 #define WG_IMAGE_PER_POL 0 /* output float [n_chan][n_pol][N][N]                      */
 #define WG_IMAGE_STOKES_I 1 /* output float [n_chan][N][N]: mean of pols 0 and P-1     */
+#define WG_IMAGE_STOKES_LINEAR 4   /* float [n_chan][S][N][N], feeds XX XY YX YY: S = 4:    */
+                                   /* I = (XX+YY)/2, Q = (XX-YY)/2, U = (XY+YX)/2,          */
+                                   /* V = -j(XY-YX)/2; n_pol 2 (XX YY): I, Q; n_pol 1: I    */
+#define WG_IMAGE_STOKES_CIRCULAR 5 /* feeds RR RL LR LL: I = (RR+LL)/2, Q = (RL+LR)/2,      */
+                                   /* U = -j(RL-LR)/2, V = (RR-LL)/2; n_pol 2 (RR LL): I, V */
+                                   /* (Algorithm "finalizer" step 2; each polarisation's   */
+                                   /* complex image divided by its own N_p, real part kept) */
 #define WG_IMAGE_PER_POL_RAW 2 /* as PER_POL without the division by N_p               */
 #define WG_IMAGE_TRANSPOSE 3 /* reads image_out (float [n_chan][n_pol][N][N]) and      */
                              /* OVERWRITES the grid with the exact transpose of mode 2:  */
@@ -306,7 +318,8 @@ int grid_autotune(wg_grid* grid, const wg_table* table, wg_worklist* wl, const w
 
 /* A7 (not in the thesis): for every input record, m_p = sum_ij conj(C_k[i][j]) grid_p(y0+i,
  * x0+j), conjugated back where psi = -1; WG_DEGRID_ADJOINT also multiplies by eps (1-f).
- * Records that are not griddable get 0.  `in` and `wl` must be the batch given to the
+ * After a vis_compress with WG_PREP_CROSS_SWAP, pols 1 and 2 of a psi = -1 record come from
+ * grid pols 2 and 1.  Records that are not griddable get 0.  `in` and `wl` must be the batch given to the
  * last vis_compress on `wl`.  vis_out: device complex64 [n_rows][n_chan][n_pol],
  * overwritten.  Errors: INVALID_ARG, SHAPE, CUDA. */
 int degrid_vis(const wg_grid* grid, const wg_table* table, const wg_vis_in* in,
@@ -315,7 +328,9 @@ int degrid_vis(const wg_grid* grid, const wg_table* table, const wg_vis_in* in,
 /* A9, Algorithm "finalizer": inverse FFT per polarisation (cuFFT, FP32, centred so that
  * image pixel N/2 is l = 0), real part, divide by N_p, by the taper psi_0(c, 2 du l)
  * psi_0(c, 2 du m) and by sinc(pi l du / beta) sinc(pi m du / beta), l = (k - N/2)/(N du).
- * image_out: device float, layout per `mode`.  The grid is not modified, except by
+ * The Stokes modes keep each polarisation's complex image, divide it by its own N_p and
+ * combine (step 2); for n_pol = 4 they are exact for V only after a vis_compress with
+ * WG_PREP_CROSS_SWAP.  image_out: device float, layout per `mode`.  The grid is not modified, except by
  * WG_IMAGE_TRANSPOSE, which reads image_out and writes the grid (see the mode list).
  * Errors: INVALID_ARG, SHAPE, CUDA. */
 int grid_correct(wg_grid* grid, const wg_table* table, int32_t mode, float* image_out,

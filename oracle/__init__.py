@@ -35,7 +35,7 @@ from .pswf import psi0
 from .table import Table, build_table, delta_table
 from .place import place, classify, Placement
 from .grid import grid_plain, grid_compressed, compress, normaliser, stats, degrid, weighted_vis
-from .correct import grid_correct, taper_1d
+from .correct import grid_correct, grid_correct_stokes, taper_1d
 from .dft import dirty_image
 from . import model
 

@@ -25,7 +25,7 @@ def _load():
     so.or_grid.restype = None
     so.or_degrid.argtypes = [i64, P, P, P, P, P, i32, i32, P, P, P]
     so.or_degrid.restype = None
-    so.or_compress.argtypes = [i64, i32, i32, i32, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
+    so.or_compress.argtypes = [i64, i32, i32, i32, i32, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
     so.or_compress.restype = i64
     return so
 

@@ -6,6 +6,11 @@ compress         : the compression of Sec. 4.3.3 with eqs. "compress1"/"conjugat
 grid_compressed  : grids the compressed list; equals grid_plain up to rounding.
 normaliser       : eq. "normalizer" (Sec. 4.3.2), N_p per channel.
 
+cross_swap=True is full-Stokes gridding: a take-conjugate (psi = -1) quad-pol record feeds
+polarisation 1 from polarisation 2 and 2 from 1, because conj(V_XY(u)) = V_YX(-u).  The thesis
+conjugates each polarisation in place (eq. "conjugatetake"), exact for the parallel hands and
+for U = (XY + YX)/2 but not for V.
+
 interleave=True is channel interleaving (Sec. 5.4, batch 1: the channels of a record row are
 interleaved and all records gridded onto one grid, as in multi-frequency synthesis): the grid
 has one channel, a record's predecessor for compression is the previous record in natural
@@ -24,12 +29,22 @@ def _p(a):
     return a.ctypes.data
 
 
-def weighted_vis(pl, vis, weight, flag) -> np.ndarray:
+def _swap_cross(a, pl, cross_swap):
+    """Swaps polarisations 1 and 2 of the take-conjugate quad-pol records (cross_swap)."""
+    if not cross_swap or a.shape[-1] != 4:
+        return a
+    b = a.copy()
+    neg = pl.psi < 0
+    b[neg, 1], b[neg, 2] = a[neg, 2], a[neg, 1]
+    return b
+
+
+def weighted_vis(pl, vis, weight, flag, cross_swap=False) -> np.ndarray:
     """q_{i,p} = eps (1-f) * vis, conjugated where psi = -1 (eq. "conjugatetake"); [rows*C, P]."""
     P = np.asarray(vis).shape[-1]
     v = np.asarray(vis, dtype=np.complex128).reshape(-1, P)
     wf = np.asarray(weight, np.float64).reshape(-1, P) * (1.0 - np.asarray(flag, np.float64).reshape(-1, P))
-    q = wf * v
+    q = _swap_cross(wf * v, pl, cross_swap)
     return np.where((pl.psi < 0)[:, None], np.conj(q), q)
 
 
@@ -49,16 +64,16 @@ def _grid_chan(pl, interleave):
     return (np.zeros_like(pl.chan), 1) if interleave else (pl.chan, pl.C)
 
 
-def grid_plain(pl, table, vis, weight, flag, n_grid, interleave=False):
+def grid_plain(pl, table, vis, weight, flag, n_grid, interleave=False, cross_swap=False):
     """grid[c][y][x][p] = sum over griddable records of q_{i,p} * K_i (eq. "gridding")."""
     P = np.asarray(vis).shape[-1]
-    q = weighted_vis(pl, vis, weight, flag)
+    q = weighted_vis(pl, vis, weight, flag, cross_swap)
     sel = pl.griddable
     chan, C = _grid_chan(pl, interleave)
     return _grid_records(sel, chan, pl.x0, pl.y0, pl.z, pl.S, q[sel], P, n_grid, C, table)
 
 
-def compress(pl, vis, weight, flag, interleave=False):
+def compress(pl, vis, weight, flag, interleave=False, cross_swap=False):
     """Returns (g, c, list_rec, list_last, gamma) following the sequential compression."""
     rows, C = pl.rows, pl.C
     P = np.asarray(vis).shape[-1]
@@ -77,24 +92,26 @@ def compress(pl, vis, weight, flag, interleave=False):
     lrec = np.zeros(n, np.int64)
     llast = np.zeros(n, np.int64)
     gamma = np.zeros((n, P), np.complex128)
-    ne = lib.or_compress(rows, C, P, 1 if interleave else 0, _p(gd), _p(x0), _p(y0), _p(z), _p(psi), _p(v), _p(w), _p(f),
+    ne = lib.or_compress(rows, C, P, 1 if interleave else 0, 1 if cross_swap else 0, _p(gd), _p(x0), _p(y0), _p(z), _p(psi), _p(v), _p(w), _p(f),
                          _p(g), _p(c), _p(head), _p(lrec), _p(llast), _p(gamma))
     return (g.astype(bool), c.astype(bool), lrec[:ne].copy(), llast[:ne].copy(), gamma[:ne].copy())
 
 
-def grid_compressed(pl, table, vis, weight, flag, n_grid, interleave=False):
+def grid_compressed(pl, table, vis, weight, flag, n_grid, interleave=False, cross_swap=False):
     P = np.asarray(vis).shape[-1]
-    g, c, lrec, llast, gamma = compress(pl, vis, weight, flag, interleave)
+    g, c, lrec, llast, gamma = compress(pl, vis, weight, flag, interleave, cross_swap)
     chan, C = _grid_chan(pl, interleave)
     return _grid_records(lrec, chan, pl.x0, pl.y0, pl.z, pl.S, gamma, P, n_grid, C, table)
 
 
-def normaliser(pl, table, weight, flag, interleave=False) -> np.ndarray:
+def normaliser(pl, table, weight, flag, interleave=False, cross_swap=False) -> np.ndarray:
     """N[c][p] = sum_i eps (g+c)(1-f) zeta_i  (eq. "normalizer"); (g+c) = griddable.
-    Interleaved: one row, the sum over all records."""
+    Interleaved: one row, the sum over all records.  With cross_swap, the weights of the
+    polarisation each record feeds."""
     rows, C = pl.rows, pl.C
     P = np.asarray(weight).shape[-1]
     wf = np.asarray(weight, np.float64).reshape(-1, P) * (1.0 - np.asarray(flag, np.float64).reshape(-1, P))
+    wf = _swap_cross(wf, pl, cross_swap)
     zeta = np.where(pl.griddable, table.zeta[np.maximum(pl.zeta_idx, 0)], 0.0)
     contrib = wf * zeta[:, None]
     chan, C = _grid_chan(pl, interleave)
@@ -111,7 +128,8 @@ def stats(pl, g, c):
             "updates": int((S2 * g).sum()), "updates_saved": int((S2 * c).sum())}
 
 
-def degrid(pl, table, grid, weight=None, flag=None, adjoint=False, interleave=False) -> np.ndarray:
+def degrid(pl, table, grid, weight=None, flag=None, adjoint=False, interleave=False,
+           cross_swap=False) -> np.ndarray:
     """Per record: m_p = sum_ij conj(K) grid_p over the footprint, conjugated back where
     psi = -1.  adjoint=True also applies eps (1 - f), giving the exact adjoint of the
     vis -> grid map.  Non-griddable records get 0.  Returns complex128 [rows*C, P]."""
@@ -128,6 +146,7 @@ def degrid(pl, table, grid, weight=None, flag=None, adjoint=False, interleave=Fa
     m = np.where((pl.psi[sel] < 0)[:, None], np.conj(m), m)
     out = np.zeros((pl.rows * pl.C, P), np.complex128)
     out[sel] = m
+    out = _swap_cross(out, pl, cross_swap)      # the adjoint of the swap is the swap
     if adjoint:
         wf = np.asarray(weight, np.float64).reshape(-1, P) * (1.0 - np.asarray(flag, np.float64).reshape(-1, P))
         out = out * wf

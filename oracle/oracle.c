@@ -74,6 +74,10 @@ void or_degrid(int64_t n, const int32_t* chan, const int32_t* x0, const int32_t*
  * Compression (Sec. 4.3.3 "Compression", eq. "ci"; Algorithms "compressindex" and the
  * "Compress and Weigh Visibilities" operator, eqs. "compress1"/"conjugatetake").
  *
+ * cross_swap (full-Stokes gridding): a conjugated quad-pol record also swaps its cross hands,
+ * since conj(V_XY(u)) is V_YX(-u); the thesis conjugates each polarisation in place, which is
+ * exact for the parallel hands and for U = (XY + YX)/2 but flips the sign of V's contribution.
+ *
  * Records are visited per channel in row order (row = baseline-major, time-minor), or,
  * with channel interleaving (the thesis's multi-frequency synthesis onto one grid, Sec. 5.4
  * batch 1), as one sequence in natural record order i = row*C + chan.  Record i is
@@ -92,7 +96,8 @@ void or_degrid(int64_t n, const int32_t* chan, const int32_t* x0, const int32_t*
  * Entries are ordered channel-major, then row (interleaved: by record).  Returns the number
  * of entries.
  */
-int64_t or_compress(int64_t rows, int32_t C, int32_t P, int32_t interleave, const uint8_t* griddable,
+int64_t or_compress(int64_t rows, int32_t C, int32_t P, int32_t interleave, int32_t cross_swap,
+                    const uint8_t* griddable,
                     const int32_t* x0, const int32_t* y0, const int64_t* z, const int8_t* psi,
                     const float* vis /* [rows][C][P][2] */, const float* weight, const uint8_t* flag,
                     uint8_t* g, uint8_t* c, int64_t* head_of, int64_t* list_rec, int64_t* list_last,
@@ -127,7 +132,10 @@ int64_t or_compress(int64_t rows, int32_t C, int32_t P, int32_t interleave, cons
             head_of[i] = cur;
             list_last[cur] = i;
             for (int32_t p = 0; p < P; ++p) {
-                const int64_t e = i * P + p;
+                /* with cross_swap, a conjugated quad-pol record feeds pol 1 from pol 2 and pol 2
+                   from pol 1: the conjugate of one cross hand is the other at -u */
+                const int32_t ps = (cross_swap && psi[i] < 0 && P == 4 && (p == 1 || p == 2)) ? 3 - p : p;
+                const int64_t e = i * P + ps;
                 const double wf = (1.0 - (double)flag[e]) * (double)weight[e];
                 gamma[2 * (cur * P + p)] += wf * (double)vis[2 * e];
                 gamma[2 * (cur * P + p) + 1] += (double)psi[i] * wf * (double)vis[2 * e + 1];

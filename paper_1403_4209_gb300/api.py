@@ -22,6 +22,9 @@ IMAGE_PER_POL = CONST["WG_IMAGE_PER_POL"]
 IMAGE_STOKES_I = CONST["WG_IMAGE_STOKES_I"]
 IMAGE_PER_POL_RAW = CONST["WG_IMAGE_PER_POL_RAW"]
 IMAGE_TRANSPOSE = CONST["WG_IMAGE_TRANSPOSE"]
+IMAGE_STOKES_LINEAR = CONST["WG_IMAGE_STOKES_LINEAR"]
+IMAGE_STOKES_CIRCULAR = CONST["WG_IMAGE_STOKES_CIRCULAR"]
+PREP_CROSS_SWAP = CONST["WG_PREP_CROSS_SWAP"]
 PREP_COMPRESS = CONST["WG_PREP_COMPRESS"]
 PREP_UNWEIGHTED = CONST["WG_PREP_UNWEIGHTED"]
 PREP_INTERLEAVE = CONST["WG_PREP_INTERLEAVE"]
@@ -260,11 +263,12 @@ class WorkList:
 
 
 def vis_compress(grid: Grid, table: ConvTable, batch: VisBatch, worklist: WorkList, compress: bool = True,
-                 unweighted: bool = False, interleave: bool = False, stream=None):
+                 unweighted: bool = False, interleave: bool = False, cross_swap: bool = False, stream=None):
     """Preparation phase.  interleave: all channels of the batch grid onto the one-channel
-    `grid` in natural record order, compressing across channels (WG_PREP_INTERLEAVE)."""
+    `grid` in natural record order, compressing across channels (WG_PREP_INTERLEAVE).
+    cross_swap: full-Stokes gridding of quad-pol data (WG_PREP_CROSS_SWAP)."""
     flags = ((PREP_COMPRESS if compress else 0) | (PREP_UNWEIGHTED if unweighted else 0)
-             | (PREP_INTERLEAVE if interleave else 0))
+             | (PREP_INTERLEAVE if interleave else 0) | (PREP_CROSS_SWAP if cross_swap else 0))
     check(lib.vis_compress(grid.handle, table.handle, ctypes.byref(batch.struct), flags,
                            worklist.handle, _stream(stream)), "vis_compress")
 

@@ -338,8 +338,10 @@ int vis_compress(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, int
     if (in->n_chan != w.C || in->n_pol != w.P) return fail(WG_E_SHAPE, "work list was created for %d channels, %d pols", w.C, w.P);
     if (in->n_rows * (int64_t)in->n_chan > w.cap)
         return fail(WG_E_CAPACITY, "%lld records exceed the work list capacity %lld", (long long)(in->n_rows * (int64_t)in->n_chan), (long long)w.cap);
-    if (flags & ~(WG_PREP_COMPRESS | WG_PREP_UNWEIGHTED | WG_PREP_INTERLEAVE))
+    if (flags & ~(WG_PREP_COMPRESS | WG_PREP_UNWEIGHTED | WG_PREP_INTERLEAVE | WG_PREP_CROSS_SWAP))
         return fail(WG_E_INVALID_ARG, "unknown vis_compress flags %d", flags);
+    if ((flags & WG_PREP_CROSS_SWAP) && in->n_pol != 4)
+        return fail(WG_E_INVALID_ARG, "WG_PREP_CROSS_SWAP needs n_pol = 4 (got %d)", in->n_pol);
     return launch_prep(th->t, gh->g, *in, flags, w, S(stream));
 }
 
@@ -507,7 +509,8 @@ int grid_correct(wg_grid* gh, const wg_table* th, int32_t mode, float* image_out
 {
     t_err[0] = 0;
     if (!gh || !th || !image_out) return fail(WG_E_INVALID_ARG, "grid_correct: null argument");
-    if (mode < WG_IMAGE_PER_POL || mode > WG_IMAGE_TRANSPOSE) return fail(WG_E_INVALID_ARG, "unknown image mode %d", mode);
+    if (mode < WG_IMAGE_PER_POL || mode > WG_IMAGE_STOKES_CIRCULAR)
+        return fail(WG_E_INVALID_ARG, "unknown image mode %d", mode);
     if (std::fabs(th->t.du - gh->g.du) > 1e-12 * gh->g.du) return fail(WG_E_SHAPE, "table du differs from grid du");
     return launch_correct(gh->g, th->t, mode, image_out, S(stream));
 }

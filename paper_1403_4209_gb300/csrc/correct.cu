@@ -11,6 +11,8 @@
 //      pi (k - N/2) / (N beta).
 // The divisions are multiplications by reciprocals prepared once in FP64 and applied in FP32.
 // A polarisation whose normaliser is zero (no data) gives a zero image.
+// WG_IMAGE_STOKES_LINEAR / _CIRCULAR combine the complex per-polarisation images, each divided by
+// its own N_p, into I, Q, U, V (step 2 "convert to multiple-Stokes image and normalise").
 // WG_IMAGE_PER_POL_RAW skips the division by N_p; WG_IMAGE_TRANSPOSE applies the exact transpose
 // of that map (the adjoint of Re(inverse FFT) under the real inner product is the forward FFT of
 // the real image): grid = (-1)^(x+y) FFT_forward((-1)^(mx+my) img / (taper sinc)).
@@ -63,6 +65,30 @@ __global__ void k_finish(const float2* __restrict__ f, int N, int P, int64_t npi
     const float* in = inv_norm ? inv_norm + gch * P : nullptr;
     if (mode == WG_IMAGE_PER_POL || mode == WG_IMAGE_PER_POL_RAW) {
         for (int p = 0; p < P; ++p) img[(gch * P + p) * nn + pix] = fp[p].x * (in ? in[p] : 1.f) * cc;
+    } else if (mode == WG_IMAGE_STOKES_LINEAR || mode == WG_IMAGE_STOKES_CIRCULAR) {
+        // Stokes from the complex per-polarisation images z_p = f_p / N_p (step 2)
+        float2 z[4];
+        for (int p = 0; p < P; ++p) z[p] = make_float2(fp[p].x * in[p] * cc, fp[p].y * in[p] * cc);
+        float* o = img + (gch * P) * nn + pix;
+        if (P == 1) {
+            o[0] = z[0].x;
+        } else if (P == 2) {
+            o[0] = 0.5f * (z[0].x + z[1].x);
+            o[nn] = 0.5f * (z[0].x - z[1].x);
+        } else {
+            const float par_s = 0.5f * (z[0].x + z[3].x), par_d = 0.5f * (z[0].x - z[3].x);
+            const float crs_s = 0.5f * (z[1].x + z[2].x), crs_d = 0.5f * (z[1].y - z[2].y);   // Re(-j(z1 - z2))/2
+            o[0] = par_s;                                                                      // I
+            if (mode == WG_IMAGE_STOKES_LINEAR) {
+                o[nn] = par_d;            // Q = (XX - YY)/2
+                o[2 * nn] = crs_s;        // U = (XY + YX)/2
+                o[3 * nn] = crs_d;        // V = -j (XY - YX)/2
+            } else {
+                o[nn] = crs_s;            // Q = (RL + LR)/2
+                o[2 * nn] = crs_d;        // U = -j (RL - LR)/2
+                o[3 * nn] = par_d;        // V = (RR - LL)/2
+            }
+        }
     } else {
         const float v0 = fp[0].x * in[0] * cc;
         img[gch * nn + pix] = (P == 1) ? v0 : 0.5f * (v0 + fp[P - 1].x * in[P - 1] * cc);

@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(256, 4) k_degrid(const int4* __restrict__ entr
                                                 int N, int C, const double* __restrict__ uvw,
                                                 const float* __restrict__ weight, const uint8_t* __restrict__ flag,
                                                 int adjoint, float2* __restrict__ out, int K, int64_t n_samples,
-                                                int64_t rows, int interleave, unsigned int* __restrict__ counter,
+                                                int64_t rows, int interleave, int cross_swap,
+                                                unsigned int* __restrict__ counter,
                                                 long long* __restrict__ dropped)
 {
     const long long n = scal[0];
@@ -132,7 +133,14 @@ __global__ void __launch_bounds__(256, 4) k_degrid(const int4* __restrict__ entr
                 const bool neg = uvw[3 * row + 2] < 0.0;
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    float2 v = neg ? make_float2(acc[p].x, -acc[p].y) : acc[p];
+                    // with cross-hand swapping, output pol 1 of a take-conjugate record comes from
+                    // grid pol 2 and pol 2 from pol 1 (the adjoint of the swap is the swap)
+                    float2 a = acc[p];
+                    if constexpr (P == 4) {
+                        if (cross_swap && neg && p == 1) a = acc[2];
+                        if (cross_swap && neg && p == 2) a = acc[1];
+                    }
+                    float2 v = neg ? make_float2(a.x, -a.y) : a;
                     if (adjoint) {
                         const float wf = weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
                         v.x *= wf;
@@ -159,7 +167,8 @@ static int degrid_impl(const Grid& g, const Table& t, const wg_vis_in& in, const
     const int blocks = num_sms() * blocks_per_sm;
     k_degrid<P><<<blocks, 256, 0, s>>>(wl.entries, wl.runs, wl.scal, t.supports_d, t.data, g.data, g.n, in.n_chan,
                                        in.uvw, in.weight, in.flag, mode == WG_DEGRID_ADJOINT ? 1 : 0, out, t.K,
-                                       t.n_samples, in.n_rows, wl.interleave ? 1 : 0, wl.task_counter + 1,
+                                       t.n_samples, in.n_rows, wl.interleave ? 1 : 0, wl.cross_swap ? 1 : 0,
+                                       wl.task_counter + 1,
                                        wl.scal + 3);
     WG_LAUNCHED("k_degrid");
     return WG_OK;

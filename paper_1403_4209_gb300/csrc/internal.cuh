@@ -97,6 +97,7 @@ struct WorkList {
     int slots = kSlotsDefault;            // gridder plan: footprint points per task
     bool fixed_r = false;                 // gridder plan: R = slots / 32 for every support
     bool interleave = false;              // last batch: channels interleaved onto one grid
+    bool cross_swap = false;              // last batch: take-conjugate records swap cross hands
     // per record
     int4* rinfo = nullptr;
     uint8_t* rclass = nullptr;
@@ -132,7 +133,7 @@ constexpr int kBitG = 12, kBitC = 13, kBitNeg = 14, kBitGd = 15;
 
 // ---- launchers (defined in the .cu files) ---------------------------------------------
 struct PlaceParams {
-    int N, beta, K, lo, compress, unweighted, interleave, C, P;
+    int N, beta, K, lo, compress, unweighted, interleave, cross_swap, C, P;
     double w_max, beta_over_du;
     const int* supports;
     const int* offsets;

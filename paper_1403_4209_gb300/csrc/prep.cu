@@ -408,6 +408,13 @@ __device__ __forceinline__ float2 vis_value(const __half2* __restrict__ v, int64
     return make_float2(scale * f.x, scale * f.y);
 }
 
+// The input polarisation that grid polarisation p of a record takes: with cross-hand swapping a
+// take-conjugate quad-pol record feeds pol 1 from pol 2 and pol 2 from pol 1.
+__device__ __forceinline__ int src_pol(int p, bool neg, int cross_swap)
+{
+    return (cross_swap && neg && (p == 1 || p == 2)) ? 3 - p : p;
+}
+
 // weighted value eps (1-f) psi-conj(vis) of polarisation p of record rec, and eps (1-f)
 template <typename VT>
 __device__ __forceinline__ float2 weighted(const VT* __restrict__ vis, const float* __restrict__ weight,
@@ -424,7 +431,7 @@ __device__ __forceinline__ float2 weighted(const VT* __restrict__ vis, const flo
 template <int P>
 __device__ __forceinline__ void weighted_vec(const float2* __restrict__ vis, const float* __restrict__ weight,
                                              const uint8_t* __restrict__ flag, int64_t rec, float, bool neg,
-                                             int unweighted, float2 (&q)[P], float (&wf)[P])
+                                             int unweighted, int cross_swap, float2 (&q)[P], float (&wf)[P])
 {
     float2 v[P];
     if constexpr (P == 1) {
@@ -453,18 +460,20 @@ __device__ __forceinline__ void weighted_vec(const float2* __restrict__ vis, con
     }
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        wf[p] = unweighted ? 1.0f : w[p] * (1.0f - (float)((f >> (8 * p)) & 0xFF));
-        q[p] = make_float2(wf[p] * v[p].x, (neg ? -1.f : 1.f) * (wf[p] * v[p].y));
+        const int ps = src_pol(p, neg, cross_swap);
+        wf[p] = unweighted ? 1.0f : w[ps] * (1.0f - (float)((f >> (8 * ps)) & 0xFF));
+        q[p] = make_float2(wf[p] * v[ps].x, (neg ? -1.f : 1.f) * (wf[p] * v[ps].y));
     }
 }
 
 template <int P>
 __device__ __forceinline__ void weighted_vec(const __half2* __restrict__ vis, const float* __restrict__ weight,
                                              const uint8_t* __restrict__ flag, int64_t rec, float scale, bool neg,
-                                             int unweighted, float2 (&q)[P], float (&wf)[P])
+                                             int unweighted, int cross_swap, float2 (&q)[P], float (&wf)[P])
 {
 #pragma unroll
-    for (int p = 0; p < P; ++p) q[p] = weighted(vis, weight, flag, rec * P + p, scale, neg, unweighted, wf[p]);
+    for (int p = 0; p < P; ++p)
+        q[p] = weighted(vis, weight, flag, rec * P + src_pol(p, neg, cross_swap), scale, neg, unweighted, wf[p]);
 }
 
 // One block per tile.  Pass 1 reads the tile's griddable records in natural order (coalesced,
@@ -513,7 +522,7 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
         if (vec) {
             float2 q[P];
             float wf[P];
-            weighted_vec<P>(vis, weight, flag, rec, scale, neg, unweighted, q, wf);
+            weighted_vec<P>(vis, weight, flag, rec, scale, neg, unweighted, pp.cross_swap, q, wf);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 s_q[(size_t)p * cap + j] = q[p];
@@ -523,7 +532,8 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 float wf;
-                s_q[(size_t)p * cap + j] = weighted(vis, weight, flag, rec * P + p, scale, neg, unweighted, wf);
+                s_q[(size_t)p * cap + j] = weighted(vis, weight, flag, rec * P + src_pol(p, neg, pp.cross_swap), scale,
+                                                    neg, unweighted, wf);
                 s_w[(size_t)p * cap + j] = wf;
             }
         }
@@ -578,7 +588,8 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
                         float wf;
-                        const float2 q = weighted(vis, weight, flag, rc2 * P + p, scale, (cls2 >> 3) & 1, unweighted, wf);
+                        const float2 q = weighted(vis, weight, flag, rc2 * P + src_pol(p, (cls2 >> 3) & 1, pp.cross_swap),
+                                                  scale, (cls2 >> 3) & 1, unweighted, wf);
                         acc[p].x += q.x;
                         acc[p].y += q.y;
                         wsum[p] += wf;
@@ -610,7 +621,8 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
                         float wf;
-                        const float2 q = weighted(vis, weight, flag, rc2 * P + p, scale, (cls2 >> 3) & 1, unweighted, wf);
+                        const float2 q = weighted(vis, weight, flag, rc2 * P + src_pol(p, (cls2 >> 3) & 1, pp.cross_swap),
+                                                  scale, (cls2 >> 3) & 1, unweighted, wf);
                         acc[p].x += q.x;
                         acc[p].y += q.y;
                         wsum[p] += wf;
@@ -742,7 +754,9 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
     pp.compress = (flags & WG_PREP_COMPRESS) ? 1 : 0;
     pp.unweighted = (flags & WG_PREP_UNWEIGHTED) ? 1 : 0;
     pp.interleave = (flags & WG_PREP_INTERLEAVE) ? 1 : 0;
+    pp.cross_swap = (flags & WG_PREP_CROSS_SWAP) && P == 4 ? 1 : 0;
     wl.interleave = pp.interleave != 0;
+    wl.cross_swap = pp.cross_swap != 0;
     pp.C = C;
     pp.P = P;
     pp.w_max = t.w_max;
