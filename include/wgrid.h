@@ -316,6 +316,23 @@ int worklist_get_plan(const wg_worklist* wl, wg_plan* plan);
 int grid_autotune(wg_grid* grid, const wg_table* table, wg_worklist* wl, const wg_plan* candidates,
                   int32_t n_candidates, int32_t repeats, wg_plan* best, float* best_ms, void* stream);
 
+/* ---- uniform and robust weighting ------------------------------------------------------
+ * The thesis names the weighting schemes (Sec. 2.1, "Deconvolution and weighting schemes")
+ * and grids with natural weights only; these follow the published definitions. */
+#define WG_WEIGHT_UNIFORM 1  /* eps' = eps / W(cell)                                       */
+#define WG_WEIGHT_ROBUST 2   /* eps' = eps / (1 + W(cell) f^2), Briggs robustness R         */
+
+/* Writes new weights for the batch: W_p(cell) is the sum of eps_p (1 - f_p) over the griddable
+ * records (placed as vis_compress places them) in each grid cell (x, y) and polarisation, per
+ * grid channel (one grid with WG_PREP_INTERLEAVE in flags, the only flag read); uniform:
+ * eps'_p = eps_p / W_p (0 where W_p = 0); robust: eps'_p = eps_p / (1 + W_p f_p^2) with
+ * f_p^2 = (5 10^-robust)^2 sum eps_p (1 - f_p) / sum_cells W_p^2.  Records that are not
+ * griddable keep eps.  weight_out: device float [n_rows][n_chan][n_pol], may alias in->weight.
+ * Allocates and frees a float density grid of (grid channels) x N^2 x n_pol on `stream`
+ * (stream-ordered).  Errors: INVALID_ARG, SHAPE, OOM, CUDA. */
+int vis_weight(const wg_grid* grid, const wg_table* table, const wg_vis_in* in, int32_t scheme,
+               double robust, int32_t flags, float* weight_out, void* stream);
+
 /* A7 (not in the thesis): for every input record, m_p = sum_ij conj(C_k[i][j]) grid_p(y0+i,
  * x0+j), conjugated back where psi = -1; WG_DEGRID_ADJOINT also multiplies by eps (1-f).
  * After a vis_compress with WG_PREP_CROSS_SWAP, pols 1 and 2 of a psi = -1 record come from

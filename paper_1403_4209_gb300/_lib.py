@@ -98,6 +98,7 @@ def _load():
         "grid_autotune": (c_i32, [c_vp, c_vp, c_vp, P(Plan), c_i32, c_i32, P(Plan), P(ctypes.c_float), c_vp]),
         "degrid_vis": (c_i32, [c_vp, c_vp, P(VisIn), c_vp, c_i32, c_vp, c_vp]),
         "grid_correct": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
+        "vis_weight": (c_i32, [c_vp, c_vp, P(VisIn), c_i32, c_dbl, c_i32, c_vp, c_vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(so, name)

@@ -292,6 +292,20 @@ def grid_autotune(grid: Grid, table: ConvTable, worklist: WorkList, candidates=N
     return int(best.seg_len), int(best.slots), bool(best.flags & CONST["WG_PLAN_FIXED_R"]), float(ms.value)
 
 
+def vis_weight(grid: Grid, table: ConvTable, batch: VisBatch, scheme: str = "uniform", robust: float = 0.0,
+               interleave: bool = False, out: torch.Tensor = None, stream=None) -> torch.Tensor:
+    """Uniform or robust (Briggs) weights for the batch from the density of its griddable records
+    per grid cell (WG_WEIGHT_UNIFORM / WG_WEIGHT_ROBUST); returns float32 [rows][chan][pol]."""
+    codes = {"uniform": CONST["WG_WEIGHT_UNIFORM"], "robust": CONST["WG_WEIGHT_ROBUST"]}
+    if out is None:
+        out = torch.empty_like(batch.weight)
+    if out.dtype != torch.float32 or out.shape != batch.weight.shape or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 tensor shaped like the weights")
+    check(lib.vis_weight(grid.handle, table.handle, ctypes.byref(batch.struct), codes[scheme], float(robust),
+                         PREP_INTERLEAVE if interleave else 0, c_vp(out.data_ptr()), _stream(stream)), "vis_weight")
+    return out
+
+
 def degrid_vis(grid: Grid, table: ConvTable, batch: VisBatch, worklist: WorkList, mode: int = DEGRID_PREDICT,
                out: torch.Tensor = None, stream=None) -> torch.Tensor:
     if out is None:

@@ -491,6 +491,23 @@ int grid_autotune(wg_grid* gh, const wg_table* th, wg_worklist* wh, const wg_pla
     return WG_OK;
 }
 
+int vis_weight(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, int32_t scheme, double robust,
+               int32_t flags, float* weight_out, void* stream)
+{
+    t_err[0] = 0;
+    if (!gh || !th || !weight_out) return fail(WG_E_INVALID_ARG, "vis_weight: null argument");
+    if (scheme != WG_WEIGHT_UNIFORM && scheme != WG_WEIGHT_ROBUST)
+        return fail(WG_E_INVALID_ARG, "unknown weighting scheme %d", scheme);
+    if (!std::isfinite(robust) || std::fabs(robust) > 10.0)
+        return fail(WG_E_INVALID_ARG, "robustness %g must be finite, within +-10", robust);
+    if (flags & ~(WG_PREP_INTERLEAVE | WG_PREP_COMPRESS | WG_PREP_UNWEIGHTED | WG_PREP_CROSS_SWAP))
+        return fail(WG_E_INVALID_ARG, "unknown flags %d", flags);
+    int rc = check_vis(gh->g, th->t, in, (flags & WG_PREP_INTERLEAVE) != 0);
+    if (rc != WG_OK) return rc;
+    if (reinterpret_cast<uintptr_t>(weight_out) & 3) return fail(WG_E_INVALID_ARG, "weight_out must be 4-byte aligned");
+    return launch_weight(th->t, gh->g, *in, scheme, robust, flags & WG_PREP_INTERLEAVE, weight_out, S(stream));
+}
+
 int degrid_vis(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, const wg_worklist* wh, int32_t mode,
                void* vis_out, void* stream)
 {

@@ -148,6 +148,8 @@ int launch_prep(const Table& t, const Grid& g, const wg_vis_in& in, int flags, W
                 cudaStream_t s);
 int launch_grid(Grid& g, const Table& t, const WorkList& wl, cudaStream_t s);
 int launch_plan(const Table& t, WorkList& wl, cudaStream_t s);
+int launch_weight(const Table& t, const Grid& g, const wg_vis_in& in, int scheme, double robust, int flags,
+                  float* out, cudaStream_t s);
 int launch_degrid(const Grid& g, const Table& t, const wg_vis_in& in, const WorkList& wl, int mode,
                   float2* out, cudaStream_t s);
 int launch_correct(Grid& g, const Table& t, int mode, float* image, cudaStream_t s);

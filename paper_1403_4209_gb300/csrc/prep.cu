@@ -18,6 +18,7 @@
 //               are cut into segments of seg_len entries; each segment needs one gridder task
 //               per block of `slots` footprint points of its largest support.  The plan can be
 //               redone with other parameters (launch_plan) without repeating the preparation.
+#include <cmath>
 #include <cstdio>
 #include <type_traits>
 
@@ -728,6 +729,33 @@ static size_t compact_smem(int rpb, int C, int P)
     return cap * P * (sizeof(float2) + sizeof(float)) + (size_t)C * P * sizeof(float) + cap * sizeof(int) + cap + 16;
 }
 
+static PlaceParams place_params(const Table& t, int n, double du, int C, int P, int flags)
+{
+    PlaceParams pp;
+    pp.N = n;
+    pp.beta = t.beta;
+    pp.K = t.K;
+    pp.lo = -((t.beta - 1) / 2);
+    pp.compress = (flags & WG_PREP_COMPRESS) ? 1 : 0;
+    pp.unweighted = (flags & WG_PREP_UNWEIGHTED) ? 1 : 0;
+    pp.interleave = (flags & WG_PREP_INTERLEAVE) ? 1 : 0;
+    pp.cross_swap = (flags & WG_PREP_CROSS_SWAP) && P == 4 ? 1 : 0;
+    pp.C = C;
+    pp.P = P;
+    pp.w_max = t.w_max;
+    pp.beta_over_du = (double)t.beta / du;
+    pp.supports = t.supports_d;
+    pp.offsets = t.offsets_d;
+    pp.wbounds = t.wbounds_d;
+    pp.wbounds_f = t.wbounds_f;
+    pp.qlim = t.beta * (n / 2 + 2);
+    pp.beta_log2 = -1;
+    for (int b = 0; b < 16; ++b)
+        if (t.beta == (1 << b)) pp.beta_log2 = b;
+    pp.zeta_f = t.zeta_f;
+    return pp;
+}
+
 template <int P>
 static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int flags, WorkList& wl,
                      cudaStream_t s)
@@ -746,30 +774,9 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
     wl.n_tiles = n_tiles;
     wl.N = g.n;
 
-    PlaceParams pp;
-    pp.N = g.n;
-    pp.beta = t.beta;
-    pp.K = t.K;
-    pp.lo = -((t.beta - 1) / 2);
-    pp.compress = (flags & WG_PREP_COMPRESS) ? 1 : 0;
-    pp.unweighted = (flags & WG_PREP_UNWEIGHTED) ? 1 : 0;
-    pp.interleave = (flags & WG_PREP_INTERLEAVE) ? 1 : 0;
-    pp.cross_swap = (flags & WG_PREP_CROSS_SWAP) && P == 4 ? 1 : 0;
+    PlaceParams pp = place_params(t, g.n, g.du, C, P, flags);
     wl.interleave = pp.interleave != 0;
     wl.cross_swap = pp.cross_swap != 0;
-    pp.C = C;
-    pp.P = P;
-    pp.w_max = t.w_max;
-    pp.beta_over_du = (double)t.beta / g.du;
-    pp.supports = t.supports_d;
-    pp.offsets = t.offsets_d;
-    pp.wbounds = t.wbounds_d;
-    pp.wbounds_f = t.wbounds_f;
-    pp.qlim = t.beta * (g.n / 2 + 2);
-    pp.beta_log2 = -1;
-    for (int b = 0; b < 16; ++b)
-        if (t.beta == (1 << b)) pp.beta_log2 = b;
-    pp.zeta_f = t.zeta_f;
 
     double* lam_inv = reinterpret_cast<double*>(wl.norm_batch + (size_t)C * P);   // [C]
     double* sc = lam_inv + C;                                                     // [C]
@@ -836,6 +843,174 @@ int launch_plan(const Table& t, WorkList& wl, cudaStream_t s)
     k_seg_scan<<<1, 1024, 0, s>>>(wl.seg_nblk, wl.seg_off, wl.scal, wl.stats);
     WG_LAUNCHED("k_seg_scan");
     return WG_OK;
+}
+
+// ---- uniform and robust weighting (the thesis names the schemes, Sec. 2.1; it grids with
+// natural weights) -----------------------------------------------------------------------
+// density W_p(cell) = sum of eps_p (1 - f_p) of the griddable records in the grid cell of their
+// placement; uniform eps' = eps / W; robust (Briggs) eps' = eps / (1 + W f^2) with
+// f^2 = (5 10^-R)^2 / (sum_cells W^2 / sum eps (1 - f)).  Records that are not griddable keep eps.
+
+// the grid cell (x, y) of a griddable record, from its footprint origin
+__device__ __forceinline__ int2 cell_of(const int4& info, const int* __restrict__ supports)
+{
+    const int h = (__ldg(&supports[info.w & 0xFFF]) - 1) / 2;
+    return make_int2((info.x & 0xFFFF) + h, ((info.x >> 16) & 0xFFFF) + h);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_density(const double* __restrict__ uvw, const double* __restrict__ lam_inv,
+                                                 const double* __restrict__ sc, const float* __restrict__ lam_f,
+                                                 const float* __restrict__ sc_f, const float* __restrict__ weight,
+                                                 const uint8_t* __restrict__ flag, int64_t rows, PlaceParams pp,
+                                                 float* __restrict__ dens, double* __restrict__ sums)
+{
+    __shared__ double s_w[P];
+    if (threadIdx.x < P) s_w[threadIdx.x] = 0.0;
+    __syncthreads();
+    const int C = pp.C;
+    const int64_t n = rows * C;
+    double acc[P] = {};
+    for (int64_t rec = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; rec < n; rec += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = rec / C;
+        const int ch = (int)(rec - row * C);
+        const int4 info = place(uvw, row, row_f(uvw, row), lam_inv[ch], sc[ch], lam_f[ch], sc_f[ch], flag, rec, P, pp).info;
+        if (!((info.w >> kBitGd) & 1)) continue;
+        const int2 xy = cell_of(info, pp.supports);
+        const int gc = pp.interleave ? 0 : ch;
+        float* d = dens + (((size_t)gc * pp.N + xy.y) * pp.N + xy.x) * P;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float wf = weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
+            if (wf != 0.f) atomicAdd(d + p, wf);
+            acc[p] += wf;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        double x = acc[p];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0 && x != 0.0) atomicAdd(&s_w[p], x);
+    }
+    __syncthreads();
+    if (threadIdx.x < P && s_w[threadIdx.x] != 0.0) atomicAdd(&sums[threadIdx.x], s_w[threadIdx.x]);
+}
+
+// sums[P + p] += sum over cells of W_p^2
+template <int P>
+__global__ void __launch_bounds__(256) k_density_sq(const float* __restrict__ dens, int64_t n_cells,
+                                                    double* __restrict__ sums)
+{
+    __shared__ double s_q[P];
+    if (threadIdx.x < P) s_q[threadIdx.x] = 0.0;
+    __syncthreads();
+    double acc[P] = {};
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const double v = dens[c * P + p];
+            acc[p] += v * v;
+        }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        double x = acc[p];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0 && x != 0.0) atomicAdd(&s_q[p], x);
+    }
+    __syncthreads();
+    if (threadIdx.x < P && s_q[threadIdx.x] != 0.0) atomicAdd(&sums[P + threadIdx.x], s_q[threadIdx.x]);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_reweight(const double* __restrict__ uvw, const double* __restrict__ lam_inv,
+                                                  const double* __restrict__ sc, const float* __restrict__ lam_f,
+                                                  const float* __restrict__ sc_f, const float* __restrict__ weight,
+                                                  const uint8_t* __restrict__ flag, int64_t rows, PlaceParams pp,
+                                                  const float* __restrict__ dens, const double* __restrict__ sums,
+                                                  int scheme, double robust_f0, float* __restrict__ out)
+{
+    const int C = pp.C;
+    const int64_t n = rows * C;
+    double f2[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) f2[p] = (sums[P + p] > 0.0) ? robust_f0 * robust_f0 * sums[p] / sums[P + p] : 0.0;
+    for (int64_t rec = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; rec < n; rec += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = rec / C;
+        const int ch = (int)(rec - row * C);
+        const int4 info = place(uvw, row, row_f(uvw, row), lam_inv[ch], sc[ch], lam_f[ch], sc_f[ch], flag, rec, P, pp).info;
+        const bool gd = (info.w >> kBitGd) & 1;
+        const float* d = nullptr;
+        if (gd) {
+            const int2 xy = cell_of(info, pp.supports);
+            d = dens + ((((size_t)(pp.interleave ? 0 : ch)) * pp.N + xy.y) * pp.N + xy.x) * P;
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float w = weight[rec * P + p];
+            float o = w;
+            if (gd) {
+                const double W = d[p];
+                if (scheme == WG_WEIGHT_UNIFORM) o = (W > 0.0) ? (float)((double)w / W) : 0.f;
+                else o = (float)((double)w / (1.0 + W * f2[p]));
+            }
+            out[rec * P + p] = o;
+        }
+    }
+}
+
+template <int P>
+static int weight_impl(const Table& t, const Grid& g, const wg_vis_in& in, int scheme, double robust, int flags,
+                       float* out, cudaStream_t s)
+{
+    const int C = in.n_chan;
+    const int64_t rows = in.n_rows;
+    PlaceParams pp = place_params(t, g.n, g.du, C, P, flags);
+    const int gc = pp.interleave ? 1 : C;
+    const int64_t n_cells = (int64_t)gc * g.n * g.n;
+    const size_t bytes = sizeof(float) * (size_t)n_cells * P + sizeof(double) * (4 * C + 2 * P);
+    void* scratch = nullptr;
+    if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(WG_E_OOM, "cannot allocate the weight-density grid (%zu bytes)", bytes);
+    }
+    float* dens = static_cast<float*>(scratch);
+    double* lam_inv = reinterpret_cast<double*>(dens + (size_t)n_cells * P);
+    double* sc = lam_inv + C;
+    double* sums = sc + C;                                   // [2P]: sum eps (1-f), sum W^2
+    float* lam_f = reinterpret_cast<float*>(sums + 2 * P);
+    float* sc_f = lam_f + C;
+    int rc = WG_OK;
+    if (cudaMemsetAsync(scratch, 0, sizeof(float) * (size_t)n_cells * P, s) != cudaSuccess ||
+        cudaMemsetAsync(sums, 0, sizeof(double) * 2 * P, s) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "weight density");
+    } else {
+        k_chan_scale<<<(C + 127) / 128, 128, 0, s>>>(in.freq_hz, C, pp.beta_over_du, lam_inv, sc, lam_f, sc_f);
+        WG_LAUNCHED("k_chan_scale");
+        const int blocks = num_sms() * 8;
+        if (rows > 0) {
+            k_density<P><<<blocks, 256, 0, s>>>(in.uvw, lam_inv, sc, lam_f, sc_f, in.weight, in.flag, rows, pp, dens, sums);
+            WG_LAUNCHED("k_density");
+            k_density_sq<P><<<blocks, 256, 0, s>>>(dens, n_cells, sums);
+            WG_LAUNCHED("k_density_sq");
+            k_reweight<P><<<blocks, 256, 0, s>>>(in.uvw, lam_inv, sc, lam_f, sc_f, in.weight, in.flag, rows, pp, dens,
+                                                 sums, scheme, 5.0 * std::pow(10.0, -robust), out);
+            WG_LAUNCHED("k_reweight");
+        }
+        if (cudaGetLastError() != cudaSuccess) rc = fail(WG_E_CUDA, "weighting kernels failed to launch");
+    }
+    cudaFreeAsync(scratch, s);
+    return rc;
+}
+
+int launch_weight(const Table& t, const Grid& g, const wg_vis_in& in, int scheme, double robust, int flags,
+                  float* out, cudaStream_t s)
+{
+    switch (in.n_pol) {
+        case 1: return weight_impl<1>(t, g, in, scheme, robust, flags, out, s);
+        case 2: return weight_impl<2>(t, g, in, scheme, robust, flags, out, s);
+        case 4: return weight_impl<4>(t, g, in, scheme, robust, flags, out, s);
+        default: return fail(WG_E_INVALID_ARG, "n_pol must be 1, 2 or 4 (got %d)", in.n_pol);
+    }
 }
 
 int launch_prep(const Table& t, const Grid& g, const wg_vis_in& in, int flags, WorkList& wl, cudaStream_t s)
