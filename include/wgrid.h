@@ -63,6 +63,9 @@ extern "C" {
 
 /* support modes of conv_table_build */
 #define WG_SUPPORT_THRESHOLD 0  /* outermost sample with |C| > threshold (Sec. 4.2.3) */
+#define WG_TABLE_WSTACK 256      /* OR-ed into support_mode: w-stacking table (Sec. 2.2.2,  */
+                                 /* eq. "stacking"): every plane holds the w = 0 kernel,   */
+                                 /* the planes and their w_k are the w-projection ones     */
 #define WG_SUPPORT_PRESCRIBED 1 /* trim or zero-pad to given supports ("normal" mode,
                                    Sec. 4.2.1), one odd support per w-plane          */
 
@@ -81,6 +84,12 @@ extern "C" {
                              /* since conj(V_XY(u)) = V_YX(-u); the thesis conjugates in */
                              /* place (eq. "conjugatetake"), exact for the parallel      */
                              /* hands and U but not for V.  N_p and degridding follow.   */
+#define WG_PREP_WSTACK 16    /* w-stacking (Sec. 2.2.2, eq. "stacking"; needs a table    */
+                             /* built with WG_TABLE_WSTACK): record (r, c) in plane k    */
+                             /* grids onto grid channel c * K + k of a grid with n_chan  */
+                             /* x K channels; N_p of channel c is kept in grid channel   */
+                             /* c * K (the other planes' N_p stay 0); not combined with  */
+                             /* WG_PREP_INTERLEAVE                                       */
 #define WG_PREP_INTERLEAVE 4 /* channel interleaving (Sec. 5.4, batch 1): the records of */
                              /* all channels, in natural order row * n_chan + chan, grid */
                              /* onto a one-channel grid (multi-frequency synthesis), and */
@@ -93,6 +102,10 @@ extern "C" {
 #define WG_IMAGE_STOKES_LINEAR 4   /* float [n_chan][S][N][N], feeds XX XY YX YY: S = 4:    */
                                    /* I = (XX+YY)/2, Q = (XX-YY)/2, U = (XY+YX)/2,          */
                                    /* V = -j(XY-YX)/2; n_pol 2 (XX YY): I, Q; n_pol 1: I    */
+#define WG_IMAGE_WSTACK 6   /* w-stacking finaliser: float [n_chan / K][P][N][N]; for each */
+                            /* input channel c, sum over planes k of the inverse FFT of   */
+                            /* grid channel c*K + k times exp(+j2pi w_k (n-1)) (zero where */
+                            /* l^2 + m^2 >= 1), real part, / N_p, / taper, / sinc        */
 #define WG_IMAGE_STOKES_CIRCULAR 5 /* feeds RR RL LR LL: I = (RR+LL)/2, Q = (RL+LR)/2,      */
                                    /* U = -j(RL-LR)/2, V = (RR-LL)/2; n_pol 2 (RR LL): I, V */
                                    /* (Algorithm "finalizer" step 2; each polarisation's   */
@@ -142,7 +155,7 @@ typedef struct wg_table_desc {
     int32_t taper_support; /* S0: the prolate spheroidal taper has bandwidth c = pi S0 / 2 */
     int32_t n_k;           /* image-plane patch side N_k (even, >= 8); 0 = max(64, next    */
                            /* power of two >= 2 * largest support) or 256 (threshold mode) */
-    int32_t support_mode;  /* WG_SUPPORT_THRESHOLD or WG_SUPPORT_PRESCRIBED               */
+    int32_t support_mode;  /* WG_SUPPORT_THRESHOLD or WG_SUPPORT_PRESCRIBED, | WG_TABLE_WSTACK*/
     int32_t store_dtype;   /* WG_F32, WG_BF16 or WG_F16: samples the gridder reads        */
     double w_max;          /* largest |w| in wavelengths (> 0 if K > 1)                    */
     double du;             /* cell size in wavelengths; must equal the grid's              */

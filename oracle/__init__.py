@@ -37,7 +37,7 @@ from .place import place, classify, Placement
 from .grid import grid_plain, grid_compressed, compress, normaliser, stats, degrid, weighted_vis
 from .correct import grid_correct, grid_correct_stokes, taper_1d
 from .dft import dirty_image
-from . import model, weighting
+from . import model, weighting, wstack
 
 __all__ = [
     "psi0", "Table", "build_table", "delta_table", "place", "classify", "Placement",

@@ -25,6 +25,8 @@ IMAGE_TRANSPOSE = CONST["WG_IMAGE_TRANSPOSE"]
 IMAGE_STOKES_LINEAR = CONST["WG_IMAGE_STOKES_LINEAR"]
 IMAGE_STOKES_CIRCULAR = CONST["WG_IMAGE_STOKES_CIRCULAR"]
 PREP_CROSS_SWAP = CONST["WG_PREP_CROSS_SWAP"]
+PREP_WSTACK = CONST["WG_PREP_WSTACK"]
+IMAGE_WSTACK = CONST["WG_IMAGE_WSTACK"]
 PREP_COMPRESS = CONST["WG_PREP_COMPRESS"]
 PREP_UNWEIGHTED = CONST["WG_PREP_UNWEIGHTED"]
 PREP_INTERLEAVE = CONST["WG_PREP_INTERLEAVE"]
@@ -127,12 +129,14 @@ class ConvTable:
     @classmethod
     def build(cls, du: float, n_wplanes: int = 1, w_max: float = 0.0, oversample: int = 8,
               taper_support: int = 7, supports=None, n_k: int = 0, threshold: float = 1e-3, store: str = "f32",
-              stream=None):
+              stacking: bool = False, stream=None):
+        """stacking: a w-stacking table (every plane holds the w = 0 kernel; WG_TABLE_WSTACK)."""
         sup_arr = None
         if supports is not None:
             sup_arr = (ctypes.c_int32 * n_wplanes)(*[int(s) for s in supports])
         d = TableDesc(int(n_wplanes), int(oversample), int(taper_support), int(n_k),
-                      SUPPORT_PRESCRIBED if supports is not None else SUPPORT_THRESHOLD,
+                      (SUPPORT_PRESCRIBED if supports is not None else SUPPORT_THRESHOLD)
+                      | (CONST["WG_TABLE_WSTACK"] if stacking else 0),
                       cls.STORES[store], float(w_max), float(du), float(threshold),
                       ctypes.cast(sup_arr, ctypes.POINTER(ctypes.c_int32)) if sup_arr is not None else None)
         h = c_vp()
@@ -263,12 +267,15 @@ class WorkList:
 
 
 def vis_compress(grid: Grid, table: ConvTable, batch: VisBatch, worklist: WorkList, compress: bool = True,
-                 unweighted: bool = False, interleave: bool = False, cross_swap: bool = False, stream=None):
+                 unweighted: bool = False, interleave: bool = False, cross_swap: bool = False, wstack: bool = False,
+                 stream=None):
     """Preparation phase.  interleave: all channels of the batch grid onto the one-channel
     `grid` in natural record order, compressing across channels (WG_PREP_INTERLEAVE).
-    cross_swap: full-Stokes gridding of quad-pol data (WG_PREP_CROSS_SWAP)."""
+    cross_swap: full-Stokes gridding of quad-pol data (WG_PREP_CROSS_SWAP).
+    wstack: w-stacking onto n_chan x K grid channels (WG_PREP_WSTACK, a stacking table)."""
     flags = ((PREP_COMPRESS if compress else 0) | (PREP_UNWEIGHTED if unweighted else 0)
-             | (PREP_INTERLEAVE if interleave else 0) | (PREP_CROSS_SWAP if cross_swap else 0))
+             | (PREP_INTERLEAVE if interleave else 0) | (PREP_CROSS_SWAP if cross_swap else 0)
+             | (PREP_WSTACK if wstack else 0))
     check(lib.vis_compress(grid.handle, table.handle, ctypes.byref(batch.struct), flags,
                            worklist.handle, _stream(stream)), "vis_compress")
 
@@ -321,7 +328,12 @@ def grid_correct(grid: Grid, table: ConvTable, mode: int = IMAGE_PER_POL, out: t
                  stream=None) -> torch.Tensor:
     if mode == IMAGE_TRANSPOSE:
         raise ValueError("use image_to_grid for the transpose mode")
-    shape = (grid.n_chan, grid.n, grid.n) if mode == IMAGE_STOKES_I else (grid.n_chan, grid.n_pol, grid.n, grid.n)
+    if mode == IMAGE_STOKES_I:
+        shape = (grid.n_chan, grid.n, grid.n)
+    elif mode == IMAGE_WSTACK:
+        shape = (grid.n_chan // table.n_wplanes, grid.n_pol, grid.n, grid.n)
+    else:
+        shape = (grid.n_chan, grid.n_pol, grid.n, grid.n)
     if out is None:
         out = torch.empty(shape, dtype=torch.float32, device=grid.data.device)
     if out.dtype != torch.float32 or tuple(out.shape) != shape or not out.is_contiguous():

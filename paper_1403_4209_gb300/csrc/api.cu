@@ -145,13 +145,15 @@ int conv_table_build(const wg_table_desc* d, wg_table** out, void* stream)
     if (d->n_wplanes > 1 && !(d->w_max > 0.0)) return fail(WG_E_INVALID_ARG, "w_max must be positive with more than one w-plane");
     if (d->store_dtype != WG_F32 && d->store_dtype != WG_BF16 && d->store_dtype != WG_F16)
         return fail(WG_E_INVALID_ARG, "store_dtype %d not supported", d->store_dtype);
-    if (d->support_mode == WG_SUPPORT_PRESCRIBED) {
+    if ((d->support_mode & ~(WG_TABLE_WSTACK | 0xFF)) != 0) return fail(WG_E_INVALID_ARG, "unknown support_mode %d", d->support_mode);
+    const int smode = d->support_mode & 0xFF;
+    if (smode == WG_SUPPORT_PRESCRIBED) {
         if (!d->supports) return fail(WG_E_INVALID_ARG, "prescribed supports missing");
         for (int k = 0; k < d->n_wplanes; ++k) {
             if (d->supports[k] < 1 || d->supports[k] % 2 == 0) return fail(WG_E_INVALID_ARG, "support %d of plane %d must be odd and positive", d->supports[k], k);
             if (d->supports[k] > kMaxSupport) return fail(WG_E_OOB_SUPPORT, "support %d of plane %d exceeds %d", d->supports[k], k, kMaxSupport);
         }
-    } else if (d->support_mode == WG_SUPPORT_THRESHOLD) {
+    } else if (smode == WG_SUPPORT_THRESHOLD) {
         if (!(d->threshold > 0.0)) return fail(WG_E_INVALID_ARG, "threshold must be positive");
     } else {
         return fail(WG_E_INVALID_ARG, "unknown support_mode %d", d->support_mode);
@@ -305,15 +307,19 @@ int worklist_create(int64_t max_records, int32_t C, int32_t P, wg_worklist** out
     return WG_OK;
 }
 
-static int check_vis(const Grid& g, const Table& t, const wg_vis_in* in, bool interleave)
+// grid channels per input channel: 1, 0 (interleaved: one grid channel), or K (w-stacking)
+static int check_vis(const Grid& g, const Table& t, const wg_vis_in* in, int per_chan)
 {
     if (!in) return fail(WG_E_INVALID_ARG, "null vis input");
     if (in->n_rows < 0) return fail(WG_E_INVALID_ARG, "n_rows must be >= 0");
-    if (interleave && (g.n_chan != 1 || in->n_pol != g.n_pol || in->n_chan < 1))
+    if (per_chan == 0 && (g.n_chan != 1 || in->n_pol != g.n_pol || in->n_chan < 1))
         return fail(WG_E_SHAPE, "interleaved channels need a one-channel grid with the vis polarisations "
                                 "(grid: %d channels, %d pols; vis: %d pols)", g.n_chan, g.n_pol, in->n_pol);
-    if (!interleave && (in->n_chan != g.n_chan || in->n_pol != g.n_pol))
-        return fail(WG_E_SHAPE, "vis shape (chan %d, pol %d) differs from the grid's (%d, %d)", in->n_chan, in->n_pol, g.n_chan, g.n_pol);
+    if (per_chan > 0 && ((int64_t)in->n_chan * per_chan != g.n_chan || in->n_pol != g.n_pol))
+        return fail(WG_E_SHAPE, "vis shape (chan %d x %d planes, pol %d) differs from the grid's (%d, %d)", in->n_chan,
+                    per_chan, in->n_pol, g.n_chan, g.n_pol);
+    if ((int64_t)in->n_chan * (per_chan > 0 ? per_chan : 1) > 65535)
+        return fail(WG_E_SHAPE, "%d channels x %d planes exceed 65535 grid channels", in->n_chan, per_chan);
     if (in->n_rows > 0 && (!in->uvw || !in->freq_hz || !in->vis || !in->weight || !in->flag))
         return fail(WG_E_INVALID_ARG, "null input array");
     if (std::fabs(t.du - g.du) > 1e-12 * g.du) return fail(WG_E_SHAPE, "table du %.17g differs from grid du %.17g", t.du, g.du);
@@ -332,14 +338,16 @@ int vis_compress(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, int
 {
     t_err[0] = 0;
     if (!gh || !th || !wh) return fail(WG_E_INVALID_ARG, "vis_compress: null handle");
-    int rc = check_vis(gh->g, th->t, in, (flags & WG_PREP_INTERLEAVE) != 0);
+    int rc = check_vis(gh->g, th->t, in, (flags & WG_PREP_INTERLEAVE) ? 0 : (flags & WG_PREP_WSTACK) ? th->t.K : 1);
     if (rc != WG_OK) return rc;
     WorkList& w = wh->w;
     if (in->n_chan != w.C || in->n_pol != w.P) return fail(WG_E_SHAPE, "work list was created for %d channels, %d pols", w.C, w.P);
     if (in->n_rows * (int64_t)in->n_chan > w.cap)
         return fail(WG_E_CAPACITY, "%lld records exceed the work list capacity %lld", (long long)(in->n_rows * (int64_t)in->n_chan), (long long)w.cap);
-    if (flags & ~(WG_PREP_COMPRESS | WG_PREP_UNWEIGHTED | WG_PREP_INTERLEAVE | WG_PREP_CROSS_SWAP))
+    if (flags & ~(WG_PREP_COMPRESS | WG_PREP_UNWEIGHTED | WG_PREP_INTERLEAVE | WG_PREP_CROSS_SWAP | WG_PREP_WSTACK))
         return fail(WG_E_INVALID_ARG, "unknown vis_compress flags %d", flags);
+    if ((flags & WG_PREP_WSTACK) && ((flags & WG_PREP_INTERLEAVE) || !th->t.stacking))
+        return fail(WG_E_INVALID_ARG, "WG_PREP_WSTACK needs a WG_TABLE_WSTACK table and no interleaving");
     if ((flags & WG_PREP_CROSS_SWAP) && in->n_pol != 4)
         return fail(WG_E_INVALID_ARG, "WG_PREP_CROSS_SWAP needs n_pol = 4 (got %d)", in->n_pol);
     return launch_prep(th->t, gh->g, *in, flags, w, S(stream));
@@ -389,7 +397,7 @@ int grid_vis(wg_grid* gh, const wg_table* th, const wg_worklist* wh, void* strea
     if (!gh || !th || !wh) return fail(WG_E_INVALID_ARG, "grid_vis: null handle");
     Grid& g = gh->g;
     const WorkList& w = wh->w;
-    if ((w.interleave ? 1 : w.C) != g.n_chan || w.P != g.n_pol)
+    if ((w.interleave ? 1 : w.C * w.wstack_k) != g.n_chan || w.P != g.n_pol)
         return fail(WG_E_SHAPE, "work list shape differs from the grid's");
     if (w.N != 0 && w.N != g.n) return fail(WG_E_SHAPE, "work list was prepared for N=%d, grid has N=%d", w.N, g.n);
     return launch_grid(g, th->t, w, S(stream));
@@ -500,9 +508,9 @@ int vis_weight(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, int32
         return fail(WG_E_INVALID_ARG, "unknown weighting scheme %d", scheme);
     if (!std::isfinite(robust) || std::fabs(robust) > 10.0)
         return fail(WG_E_INVALID_ARG, "robustness %g must be finite, within +-10", robust);
-    if (flags & ~(WG_PREP_INTERLEAVE | WG_PREP_COMPRESS | WG_PREP_UNWEIGHTED | WG_PREP_CROSS_SWAP))
+    if (flags & ~(WG_PREP_INTERLEAVE | WG_PREP_COMPRESS | WG_PREP_UNWEIGHTED | WG_PREP_CROSS_SWAP | WG_PREP_WSTACK))
         return fail(WG_E_INVALID_ARG, "unknown flags %d", flags);
-    int rc = check_vis(gh->g, th->t, in, (flags & WG_PREP_INTERLEAVE) != 0);
+    int rc = check_vis(gh->g, th->t, in, (flags & WG_PREP_INTERLEAVE) ? 0 : (flags & WG_PREP_WSTACK) ? th->t.K : 1);
     if (rc != WG_OK) return rc;
     if (reinterpret_cast<uintptr_t>(weight_out) & 3) return fail(WG_E_INVALID_ARG, "weight_out must be 4-byte aligned");
     return launch_weight(th->t, gh->g, *in, scheme, robust, flags & WG_PREP_INTERLEAVE, weight_out, S(stream));
@@ -515,7 +523,7 @@ int degrid_vis(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, const
     if (!gh || !th || !wh || !vis_out) return fail(WG_E_INVALID_ARG, "degrid_vis: null argument");
     if (mode != WG_DEGRID_PREDICT && mode != WG_DEGRID_ADJOINT) return fail(WG_E_INVALID_ARG, "unknown degrid mode %d", mode);
     const WorkList& w = wh->w;
-    int rc = check_vis(gh->g, th->t, in, w.interleave);
+    int rc = check_vis(gh->g, th->t, in, w.interleave ? 0 : w.wstack_k);
     if (rc != WG_OK) return rc;
     if (w.rows != in->n_rows || w.C != in->n_chan) return fail(WG_E_SHAPE, "work list was prepared for a different batch");
     if (reinterpret_cast<uintptr_t>(vis_out) & 7) return fail(WG_E_INVALID_ARG, "vis_out must be 8-byte aligned");
@@ -526,8 +534,11 @@ int grid_correct(wg_grid* gh, const wg_table* th, int32_t mode, float* image_out
 {
     t_err[0] = 0;
     if (!gh || !th || !image_out) return fail(WG_E_INVALID_ARG, "grid_correct: null argument");
-    if (mode < WG_IMAGE_PER_POL || mode > WG_IMAGE_STOKES_CIRCULAR)
+    if (mode < WG_IMAGE_PER_POL || mode > WG_IMAGE_WSTACK)
         return fail(WG_E_INVALID_ARG, "unknown image mode %d", mode);
+    if (mode == WG_IMAGE_WSTACK && (!th->t.stacking || gh->g.n_chan % th->t.K != 0))
+        return fail(WG_E_INVALID_ARG, "WG_IMAGE_WSTACK needs a WG_TABLE_WSTACK table and n_chan a multiple of its %d planes",
+                    th->t.K);
     if (std::fabs(th->t.du - gh->g.du) > 1e-12 * gh->g.du) return fail(WG_E_SHAPE, "table du differs from grid du");
     return launch_correct(gh->g, th->t, mode, image_out, S(stream));
 }

@@ -11,6 +11,8 @@
 //      pi (k - N/2) / (N beta).
 // The divisions are multiplications by reciprocals prepared once in FP64 and applied in FP32.
 // A polarisation whose normaliser is zero (no data) gives a zero image.
+// WG_IMAGE_WSTACK sums the planes of each channel after the inverse FFT, each multiplied by its
+// exp(+j2pi w_k (n-1)) (eq. "stacking"), then takes steps 2-4 with the channel's N_p.
 // WG_IMAGE_STOKES_LINEAR / _CIRCULAR combine the complex per-polarisation images, each divided by
 // its own N_p, into I, Q, U, V (step 2 "convert to multiple-Stokes image and normalise").
 // WG_IMAGE_PER_POL_RAW skips the division by N_p; WG_IMAGE_TRANSPOSE applies the exact transpose
@@ -108,6 +110,51 @@ __global__ void k_image_in(const float* __restrict__ img, int N, int P, int64_t 
     for (int p = 0; p < P; ++p) f[q * P + p] = make_float2(img[(gch * P + p) * nn + pix] * cc, 0.f);
 }
 
+// w-stacking (eq. "stacking"): n - 1 at every pixel, NaN outside the unit disk (l^2 + m^2 >= 1)
+__global__ void k_nm1(int N, double du, double* __restrict__ nm1)
+{
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= (int64_t)N * N) return;
+    const int my = (int)(pix / N), mx = (int)(pix - (int64_t)my * N);
+    const double l = (double)(mx - N / 2) / ((double)N * du), m = (double)(my - N / 2) / ((double)N * du);
+    const double r2 = l * l + m * m;
+    nm1[pix] = (r2 < 1.0) ? -r2 / (1.0 + sqrt(1.0 - r2)) : __longlong_as_double(0x7FF8000000000000ll);
+}
+
+// acc[p][pix] += f[pix][p] exp(+j 2 pi w_k (n - 1)) for the P polarisations of one grid channel
+// (the (-1)^(mx+my) demodulation, common to all planes, is applied at the end)
+__global__ void k_stack_acc(const float2* __restrict__ f, int P, int64_t nn, const double* __restrict__ nm1, double wk,
+                            float2* __restrict__ acc)
+{
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= nn) return;
+    const double v = nm1[pix];
+    if (!(v == v)) return;                              // outside the unit disk: screen 0
+    const double x = wk * v;
+    float sn, cs;
+    sincospif((float)(2.0 * (x - rint(x))), &sn, &cs);
+    for (int p = 0; p < P; ++p) {
+        const float2 a = f[pix * P + p];
+        float2& o = acc[p * nn + pix];
+        o.x += a.x * cs - a.y * sn;
+        o.y += a.x * sn + a.y * cs;
+    }
+}
+
+// image[c][p][pix] = Re(acc) (-1)^(mx+my) / (taper sinc)(l) / (taper sinc)(m) / N_p(c)
+__global__ void k_stack_finish(const float2* __restrict__ acc, int N, int P, int64_t npix, const float* __restrict__ icorr,
+                               const float* __restrict__ inv_norm, int K, float* __restrict__ img)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over channels x pols x pixels
+    if (q >= npix) return;
+    const int64_t nn = (int64_t)N * N;
+    const int64_t cp = q / nn, pix = q - cp * nn;
+    const int c = (int)(cp / P), p = (int)(cp - (int64_t)c * P);
+    const int my = (int)(pix / N), mx = (int)(pix - (int64_t)my * N);
+    const float cc = ((mx + my) & 1 ? -1.f : 1.f) * icorr[mx] * icorr[my];
+    img[q] = acc[q].x * cc * inv_norm[((int64_t)c * K) * P + p];
+}
+
 int launch_correct(Grid& g, const Table& t, int mode, float* image, cudaStream_t s)
 {
     const int N = g.n, P = g.n_pol, C = g.n_chan;
@@ -159,6 +206,48 @@ int launch_correct(Grid& g, const Table& t, int mode, float* image, cudaStream_t
             WG_LAUNCHED("k_modulate");
         }
         return WG_OK;
+    }
+    if (mode == WG_IMAGE_WSTACK) {
+        const int K = t.K, Cin = C / K;
+        const int64_t nn = (int64_t)N * N;
+        void* buf = nullptr;
+        const size_t acc_bytes = sizeof(float2) * (size_t)Cin * P * nn;
+        if (cudaMallocAsync(&buf, acc_bytes + sizeof(double) * (size_t)nn, s) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(WG_E_OOM, "cannot allocate the w-stacking accumulators (%zu bytes)", acc_bytes);
+        }
+        float2* acc = static_cast<float2*>(buf);
+        double* nm1 = reinterpret_cast<double*>(static_cast<char*>(buf) + acc_bytes);
+        int rc = WG_OK;
+        if (cudaMemsetAsync(acc, 0, acc_bytes, s) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "w-stacking");
+        if (rc == WG_OK) {
+            k_nm1<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(N, g.du, nm1);
+            WG_LAUNCHED("k_nm1");
+            k_inv_norm<<<(C * P + 127) / 128, 128, 0, s>>>(g.norm, C * P, g.inv_norm);
+            WG_LAUNCHED("k_inv_norm");
+        }
+        for (int c0 = 0; c0 < C && rc == WG_OK; c0 += G) {
+            k_modulate<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g.data + (size_t)c0 * per_chan, g.scratch, N, P, tot);
+            WG_LAUNCHED("k_modulate");
+            for (int p = 0; p < P && rc == WG_OK; ++p) {
+                cufftComplex* d = reinterpret_cast<cufftComplex*>(g.scratch + p);
+                if (cufftExecC2C(g.plan, d, d, CUFFT_INVERSE) != CUFFT_SUCCESS) rc = fail(WG_E_CUDA, "cufftExecC2C failed");
+            }
+            for (int gc = c0; gc < c0 + G && rc == WG_OK; ++gc) {
+                k_stack_acc<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(g.scratch + (size_t)(gc - c0) * per_chan, P, nn,
+                                                                         nm1, t.w_planes[gc % K],
+                                                                         acc + (size_t)(gc / K) * P * nn);
+                WG_LAUNCHED("k_stack_acc");
+            }
+        }
+        if (rc == WG_OK) {
+            const int64_t npix_all = (int64_t)Cin * P * nn;
+            k_stack_finish<<<(unsigned)((npix_all + 255) / 256), 256, 0, s>>>(acc, N, P, npix_all, g.icorr, g.inv_norm, K,
+                                                                              image);
+            WG_LAUNCHED("k_stack_finish");
+        }
+        cudaFreeAsync(buf, s);
+        return rc;
     }
     const bool raw = (mode == WG_IMAGE_PER_POL_RAW);
     if (!raw) {

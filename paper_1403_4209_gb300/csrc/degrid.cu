@@ -60,7 +60,7 @@ template <int P>
 __global__ void __launch_bounds__(256, 4) k_degrid(const int4* __restrict__ entries, const int2* __restrict__ runs,
                                                 const long long* __restrict__ scal, const int* __restrict__ supports,
                                                 const float2* __restrict__ table, const float2* __restrict__ grid,
-                                                int N, int C, const double* __restrict__ uvw,
+                                                int N, int C, int kst, const double* __restrict__ uvw,
                                                 const float* __restrict__ weight, const uint8_t* __restrict__ flag,
                                                 int adjoint, float2* __restrict__ out, int K, int64_t n_samples,
                                                 int64_t rows, int interleave, int cross_swap,
@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(256, 4) k_degrid(const int4* __restrict__ entr
         const long long c1 = min(n, c0 + kDegridChunk);
         for (long long e = c0; e < c1; ++e) {
             const int4 E = entries[e];
-            const int k = E.w & 0xFFF, ch = (E.w >> 16) & 0xFFFF;
+            const int k = E.w & 0xFFF, gchan = (E.w >> 16) & 0xFFFF;
+            const int ch = gchan / kst;                  // input channel (w-stacking: kst planes each)
             if (k >= K || ch >= C) {                 // device-side bounds checks (never taken)
                 if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
                 continue;
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(256, 4) k_degrid(const int4* __restrict__ entr
                 if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
                 continue;
             }
-            const float2* gch = grid + (size_t)ch * N * N * P;   // channel 0 when interleaved
+            const float2* gch = grid + (size_t)gchan * N * N * P;   // channel 0 when interleaved
             f32x2 A[P], B[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) A[p] = B[p] = 0ull;
@@ -166,6 +167,7 @@ static int degrid_impl(const Grid& g, const Table& t, const wg_vis_in& in, const
         blocks_per_sm = 1;
     const int blocks = num_sms() * blocks_per_sm;
     k_degrid<P><<<blocks, 256, 0, s>>>(wl.entries, wl.runs, wl.scal, t.supports_d, t.data, g.data, g.n, in.n_chan,
+                                       wl.wstack_k,
                                        in.uvw, in.weight, in.flag, mode == WG_DEGRID_ADJOINT ? 1 : 0, out, t.K,
                                        t.n_samples, in.n_rows, wl.interleave ? 1 : 0, wl.cross_swap ? 1 : 0,
                                        wl.task_counter + 1,

@@ -428,12 +428,13 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_grid(const int4* __restrict_
     }
 }
 
-// adds the batch normaliser and statistics into the grid's accumulators
-__global__ void k_accumulate(double* __restrict__ gnorm, const double* __restrict__ bnorm, int n,
+// adds the batch normaliser and statistics into the grid's accumulators; the batch's normaliser
+// row c goes to grid channel c * stride (w-stacking keeps a channel's N_p in its plane 0)
+__global__ void k_accumulate(double* __restrict__ gnorm, const double* __restrict__ bnorm, int n, int P, int stride,
                              unsigned long long* __restrict__ gcnt, const unsigned long long* __restrict__ bcnt)
 {
     const int i = threadIdx.x + blockIdx.x * blockDim.x;
-    if (i < n) gnorm[i] += bnorm[i];
+    if (i < n) gnorm[(size_t)(i / P) * stride * P + i % P] += bnorm[i];
     if (i < ST_N) gcnt[i] += bcnt[i];
 }
 
@@ -499,9 +500,9 @@ static int grid_impl(Grid& g, const Table& t, const WorkList& wl, cudaStream_t s
                                                             reinterpret_cast<float4*>(g.err), n4);
         WG_LAUNCHED("k_fold");
     }
-    const int n = g.n_chan * g.n_pol;
+    const int n = (g.n_chan / wl.wstack_k) * g.n_pol;     // normaliser rows of the batch
     const int m = std::max(n, (int)ST_N);
-    k_accumulate<<<(m + 255) / 256, 256, 0, s>>>(g.norm, wl.norm_batch, n, g.counters, wl.stats);
+    k_accumulate<<<(m + 255) / 256, 256, 0, s>>>(g.norm, wl.norm_batch, n, g.n_pol, wl.wstack_k, g.counters, wl.stats);
     WG_LAUNCHED("k_accumulate");
     return WG_OK;
 }

@@ -86,6 +86,8 @@ struct Table {
     float* zeta_f = nullptr;              // C-3 in FP32 (normaliser terms)
     std::vector<int> supports, offsets;   // host copies
     std::vector<double> pswf;             // Legendre coefficients of psi_0 (even degrees)
+    bool stacking = false;                // every plane holds the w = 0 kernel (w-stacking)
+    std::vector<double> w_planes;         // w_k of each plane, wavelengths
 };
 
 struct WorkList {
@@ -98,6 +100,7 @@ struct WorkList {
     bool fixed_r = false;                 // gridder plan: R = slots / 32 for every support
     bool interleave = false;              // last batch: channels interleaved onto one grid
     bool cross_swap = false;              // last batch: take-conjugate records swap cross hands
+    int wstack_k = 1;                     // last batch: w-stacking planes (1: no stacking)
     // per record
     int4* rinfo = nullptr;
     uint8_t* rclass = nullptr;
@@ -133,7 +136,7 @@ constexpr int kBitG = 12, kBitC = 13, kBitNeg = 14, kBitGd = 15;
 
 // ---- launchers (defined in the .cu files) ---------------------------------------------
 struct PlaceParams {
-    int N, beta, K, lo, compress, unweighted, interleave, cross_swap, C, P;
+    int N, beta, K, lo, compress, unweighted, interleave, cross_swap, wstack, C, P;
     double w_max, beta_over_du;
     const int* supports;
     const int* offsets;

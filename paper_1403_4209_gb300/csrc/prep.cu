@@ -546,8 +546,9 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
         const int j = s_heads[h];
         const int rr = j / C, ch = j - rr * C;
         const int64_t row = row0 + rr, rec = row * C + ch;
-        const int gch = IL ? 0 : ch;       // the grid channel and work-list list
+        const int gch = IL ? 0 : ch;       // the work-list list (and normaliser row)
         const int4 info = rinfo[rec];
+        const int ech = pp.wstack ? ch * pp.K + (info.w & 0xFFF) : gch;   // the grid channel
         const int rank = (info.w >> 16) & 0xFFFF;
         const int dst = chan_base[gch] + tile_off[tile * C + gch] + rank;
         if (dst < 0 || (int64_t)dst >= cap_entries) {   // cannot happen with a consistent scan
@@ -634,7 +635,7 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
             }
         }
         const int k = info.w & 0xFFF;
-        entries[dst] = make_int4(info.x, info.y, info.z, k | (gch << 16));
+        entries[dst] = make_int4(info.x, info.y, info.z, k | (ech << 16));
 #pragma unroll
         for (int p = 0; p < P; ++p) gamma[(int64_t)dst * P + p] = acc[p];
         // runs: first and last row of the channel, or first and last record when interleaved
@@ -740,6 +741,7 @@ static PlaceParams place_params(const Table& t, int n, double du, int C, int P, 
     pp.unweighted = (flags & WG_PREP_UNWEIGHTED) ? 1 : 0;
     pp.interleave = (flags & WG_PREP_INTERLEAVE) ? 1 : 0;
     pp.cross_swap = (flags & WG_PREP_CROSS_SWAP) && P == 4 ? 1 : 0;
+    pp.wstack = (flags & WG_PREP_WSTACK) ? 1 : 0;
     pp.C = C;
     pp.P = P;
     pp.w_max = t.w_max;
@@ -777,6 +779,7 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
     PlaceParams pp = place_params(t, g.n, g.du, C, P, flags);
     wl.interleave = pp.interleave != 0;
     wl.cross_swap = pp.cross_swap != 0;
+    wl.wstack_k = pp.wstack ? t.K : 1;
 
     double* lam_inv = reinterpret_cast<double*>(wl.norm_batch + (size_t)C * P);   // [C]
     double* sc = lam_inv + C;                                                     // [C]

@@ -253,7 +253,7 @@ int build_table(const wg_table_desc& d, Table& t, cudaStream_t s)
     t.pswf = pswf_coefficients(M_PI * d.taper_support / 2.0);
     int n_k = d.n_k;
     if (n_k == 0) {
-        if (d.support_mode == WG_SUPPORT_PRESCRIBED) {
+        if ((d.support_mode & 0xFF) == WG_SUPPORT_PRESCRIBED) {
             int smax = 1;
             for (int k = 0; k < K; ++k) smax = std::max(smax, d.supports[k]);
             n_k = default_nk(smax);
@@ -288,6 +288,11 @@ int build_table(const wg_table_desc& d, Table& t, cudaStream_t s)
     int rc = WG_OK;
     std::vector<double> wk(K);
     for (int k = 0; k < K; ++k) wk[k] = (K == 1) ? 0.0 : d.w_max * ((double)k / (K - 1)) * ((double)k / (K - 1));
+    // w-stacking: every plane holds the w = 0 kernel; the plane values w_k stay for the correction
+    t.stacking = (d.support_mode & WG_TABLE_WSTACK) != 0;
+    t.w_planes = wk;
+    std::vector<double> wscreen(K);
+    for (int k = 0; k < K; ++k) wscreen[k] = t.stacking ? 0.0 : wk[k];
     do {
         if (cudaMemcpyAsync(coef, t.pswf.data(), sizeof(double) * t.pswf.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) { rc = fail(WG_E_CUDA, "copy"); break; }
         k_taper_patch<<<(n_k + 127) / 128, 128, 0, s>>>(coef, (int)t.pswf.size(), n_k, taper);
@@ -298,7 +303,7 @@ int build_table(const wg_table_desc& d, Table& t, cudaStream_t s)
         const int nb = (int)((tot + 255) / 256);
         // supports
         t.supports.assign(K, 1);
-        if (d.support_mode == WG_SUPPORT_PRESCRIBED) {
+        if ((d.support_mode & 0xFF) == WG_SUPPORT_PRESCRIBED) {
             for (int k = 0; k < K; ++k) t.supports[k] = d.supports[k];
         } else {
             double nrm = 0;
@@ -306,7 +311,7 @@ int build_table(const wg_table_desc& d, Table& t, cudaStream_t s)
                 cudaStreamSynchronize(s) != cudaSuccess) { rc = fail(WG_E_CUDA, "norm readback"); break; }
             const double thr2 = (d.threshold * nrm) * (d.threshold * nrm);
             for (int k = 0; k < K && rc == WG_OK; ++k) {
-                k_fill_plane<<<nb, 256, 0, s>>>(taper, n_k, M, d.du, wk[k], plane);
+                k_fill_plane<<<nb, 256, 0, s>>>(taper, n_k, M, d.du, wscreen[k], plane);
                 count_launch();
                 if (cufftExecZ2Z(plan, plane, plane, CUFFT_FORWARD) != CUFFT_SUCCESS) { rc = fail(WG_E_CUDA, "cufftExecZ2Z"); break; }
                 cudaMemsetAsync(radius, 0xff, sizeof(int), s);
@@ -327,7 +332,7 @@ int build_table(const wg_table_desc& d, Table& t, cudaStream_t s)
         rc = finish_layout(t);
         if (rc != WG_OK) break;
         for (int k = 0; k < K; ++k) {
-            k_fill_plane<<<nb, 256, 0, s>>>(taper, n_k, M, d.du, wk[k], plane);
+            k_fill_plane<<<nb, 256, 0, s>>>(taper, n_k, M, d.du, wscreen[k], plane);
             count_launch();
             if (cufftExecZ2Z(plan, plane, plane, CUFFT_FORWARD) != CUFFT_SUCCESS) { rc = fail(WG_E_CUDA, "cufftExecZ2Z"); break; }
             k_trim<<<beta * beta, 256, 0, s>>>(plane, M, beta, t.supports[k], norm, t.data + t.offsets[k],
@@ -356,6 +361,9 @@ int import_table(int K, int beta, double w_max, double du, int s0, const int* su
     t.beta = beta;
     t.s0 = s0;
     t.w_max = w_max;
+    t.stacking = false;
+    t.w_planes.assign(K, 0.0);
+    for (int k = 0; k < K && K > 1; ++k) t.w_planes[k] = w_max * ((double)k / (K - 1)) * ((double)k / (K - 1));
     t.du = du;
     t.pswf = pswf_coefficients(M_PI * s0 / 2.0);
     t.supports.assign(supports, supports + K);
