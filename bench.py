@@ -44,6 +44,10 @@ WORKLOADS = {
               "baselines x 3600 steps at 1 s, 4 pols) with 16 channels 12.2 kHz apart from 150 MHz; grid 2048^2 x 1; "
               "32 sqrt(w)-spaced w-planes, supports 9..65; beta=8; FP32 table; compression over the natural "
               "record order",
+    "wstack_2k": "w-stacking: the wproj_2k geometry (2016 baselines x 3600 steps at 1 s, 4 pols) with 4 channels "
+                 "120-124 MHz; 32 sqrt(w)-spaced planes each holding the w = 0 kernel (support 9) on 2048^2 x 4 x 32 "
+                 "grids; the finaliser sums the plane images times exp(+j2pi w_k (n-1)); beta=8; FP32 table; "
+                 "compression on",
     "degrid_1k": "differentiable sky model: 1024^2 FP32 sky (4 channels x 4 pols; seeded point sources plus a "
                  "Gaussian blob) -> degridding forward, chi^2 against noisy complex64 visibilities, hand-written "
                  "adjoint gridding backward; 64 stations (3 km Gaussian), 2016 baselines x 600 steps at 6 s, "
@@ -55,13 +59,19 @@ WORKLOADS = {
 }
 # bounded CPU samples of the same geometry (channels, time steps)
 CPU_SAMPLE = {"wproj_2k": (16, 1200), "w0_small": (1, 256), "batch_8k": (2, 40), "degrid_1k": (1, 300),
-              "mfs_2k": (4, 1200)}
+              "mfs_2k": (4, 1200), "wstack_2k": (2, 1200)}
 # worker processes of the CPU baseline (one channel each) where the oracle's table build is cheap
 CPU_PROCS = {"wproj_2k": 16}
 REF_SAMPLE = {"wproj_2k": (2, 360), "w0_small": (1, 256), "batch_8k": (1, 40), "degrid_1k": (1, 60)}
-COMPRESS = {"wproj_2k": True, "w0_small": False, "batch_8k": True, "degrid_1k": True, "mfs_2k": True}
+COMPRESS = {"wproj_2k": True, "w0_small": False, "batch_8k": True, "degrid_1k": True, "mfs_2k": True,
+            "wstack_2k": True}
 # channel interleaving: every channel onto one grid, compression in natural record order
 INTERLEAVE = {"mfs_2k": True}
+# w-stacking: planes of the w = 0 kernel (support WSTACK_SUPPORT), one grid channel per plane
+WSTACK = {"wstack_2k": 32}
+WSTACK_SUPPORT = 9
+# workloads that are a slice of another geometry
+SYNTH_NAME = {"wstack_2k": ("wproj_2k", {"n_chan": 4})}
 CHAN_GROUP = {"batch_8k": 8}
 # gridder plans the autotuner tries (seg_len, slots, fixed R): on the batch for the single-grid
 # workloads, per channel group for the batched one
@@ -206,16 +216,27 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = "cuda:%d" % local_rank
-    wl = synth.make(args.workload, device=dev, n_chan=args.n_chan, n_times=args.n_times, chan0=args.chan0)
-    tab = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+    base, kw = SYNTH_NAME.get(args.workload, (args.workload, {}))
+    kw = dict(kw)
+    if args.n_chan is not None:
+        kw["n_chan"] = args.n_chan
+    wl = synth.make(base, device=dev, n_times=args.n_times, chan0=args.chan0, **kw)
+    stack_k = WSTACK.get(args.workload, 0)                 # w-stacking planes (0: w-projection)
+    if stack_k:
+        tab = wg.ConvTable.build(wl.du, stack_k, wl.w_max, wl.oversample, wl.taper_support,
+                                 supports=[WSTACK_SUPPORT] * stack_k, stacking=True)
+    else:
+        tab = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
     inter = INTERLEAVE.get(args.workload, False)
-    gc = 1 if inter else wl.n_chan                         # grid channels
+    gc = 1 if inter else wl.n_chan * max(1, stack_k)       # grid channels
     g = wg.Grid(wl.n_grid, wl.du, wl.n_pol, gc, device=dev)
     uvw_d = torch.as_tensor(wl.uvw, device=dev)
     freq_d = torch.as_tensor(wl.freq, device=dev)
     batch = wg.VisBatch(uvw_d, freq_d, wl.vis, wl.weight, wl.flag)
     wlst = wg.WorkList(wl.rows * wl.n_chan, wl.n_chan, wl.n_pol)
-    img = torch.empty((gc, wl.n_grid, wl.n_grid), dtype=torch.float32, device=dev)
+    img_mode = wg.IMAGE_WSTACK if stack_k else wg.IMAGE_STOKES_I
+    img_shape = (wl.n_chan, wl.n_pol, wl.n_grid, wl.n_grid) if stack_k else (gc, wl.n_grid, wl.n_grid)
+    img = torch.empty(img_shape, dtype=torch.float32, device=dev)
     compress = COMPRESS[args.workload]
     stream = torch.cuda.current_stream()
     ev_g = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -226,18 +247,18 @@ def run_ours(args, rank, world, local_rank):
         g.zero()
         if k is not None:
             ev_p[k][0].record(stream)
-        wg.vis_compress(g, tab, batch, wlst, compress=compress, interleave=inter)
+        wg.vis_compress(g, tab, batch, wlst, compress=compress, interleave=inter, wstack=bool(stack_k))
         if k is not None:
             ev_p[k][1].record(stream)
             ev_g[k][0].record(stream)
         wg.grid_vis(g, tab, wlst)
         if k is not None:
             ev_g[k][1].record(stream)
-        wg.grid_correct(g, tab, mode=wg.IMAGE_STOKES_I, out=img)
+        wg.grid_correct(g, tab, mode=img_mode, out=img)
 
     # one-off, outside the timed region: pick the gridder plan on this batch
     g.zero()
-    wg.vis_compress(g, tab, batch, wlst, compress=compress, interleave=inter)
+    wg.vis_compress(g, tab, batch, wlst, compress=compress, interleave=inter, wstack=bool(stack_k))
     plan = wg.grid_autotune(g, tab, wlst, candidates=STEP_PLANS, repeats=2)[:3]
 
     clocks = ClockSampler(local_rank)
@@ -270,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
 
     # precision variants (reduced-precision tables, half visibilities, compensated flushes)
     variants = {}
-    if not args.no_variants and not inter:
+    if not args.no_variants and not inter and not stack_k:
         vis_h, scale_h = synth.to_half_vis(wl.vis)
         batch_h = wg.VisBatch(uvw_d, freq_d, vis_h, wl.weight, wl.flag, vis_scale=scale_h)
         for name, store, half, comp in (("fp32+compensated", "f32", False, True), ("f16 table", "f16", False, False),
@@ -305,16 +326,31 @@ def run_ours(args, rank, world, local_rank):
     w_out = torch.empty_like(batch.weight)
     t_weight = {}
     for scheme in ("uniform", "robust"):
-        wg.vis_weight(g, tab, batch, scheme=scheme, interleave=inter, out=w_out)
+        wg.vis_weight(g, tab, batch, scheme=scheme, interleave=inter, wstack=bool(stack_k), out=w_out)
         torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
         for _ in range(3):
-            wg.vis_weight(g, tab, batch, scheme=scheme, interleave=inter, out=w_out)
+            wg.vis_weight(g, tab, batch, scheme=scheme, interleave=inter, wstack=bool(stack_k), out=w_out)
         a1.record(stream)
         torch.cuda.synchronize()
         t_weight[scheme] = a0.elapsed_time(a1) / 3
     del w_out
+
+    # the full-Stokes finaliser on the same grid (quad-pol only), timed separately
+    t_stokes = None
+    if wl.n_pol == 4 and not stack_k:
+        img4 = torch.empty((gc, 4, wl.n_grid, wl.n_grid), dtype=torch.float32, device=dev)
+        wg.grid_correct(g, tab, mode=wg.IMAGE_STOKES_LINEAR, out=img4)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(3):
+            wg.grid_correct(g, tab, mode=wg.IMAGE_STOKES_LINEAR, out=img4)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t_stokes = a0.elapsed_time(a1) / 3
+        del img4
 
     # degridding of the same batch (predict mode), timed separately
     out_v = torch.empty_like(wl.vis)
@@ -369,9 +405,9 @@ def run_ours(args, rank, world, local_rank):
             stream.wait_event(copied[k % 2])
             b = slots[k % 2][1]
             g.zero()
-            wg.vis_compress(g, tab, b, wlst, compress=compress, interleave=inter)
+            wg.vis_compress(g, tab, b, wlst, compress=compress, interleave=inter, wstack=bool(stack_k))
             wg.grid_vis(g, tab, wlst)
-            wg.grid_correct(g, tab, mode=wg.IMAGE_STOKES_I, out=img)
+            wg.grid_correct(g, tab, mode=img_mode, out=img)
             consumed[k % 2].record(stream)
             h_img.copy_(img, non_blocking=True)
 
@@ -422,6 +458,7 @@ def run_ours(args, rank, world, local_rank):
                   "prep_ms": round(t_prep, 4),
                   "weighting_uniform_ms": round(t_weight["uniform"], 3),
                   "weighting_robust_ms": round(t_weight["robust"], 3),
+                  "correct_stokes_iquv_ms": None if t_stokes is None else round(t_stokes, 3),
                   "prep_record_rate_M": round(st["records"] / (t_prep * 1e-3) / 1e6, 1),
                   "updates_real": real, "updates_total": total},
         "roofline": {"kernel": "k_grid", "bound": "alu", "achieved": round(achieved, 3),
@@ -441,7 +478,7 @@ def run_ours(args, rank, world, local_rank):
         nc, nt = CPU_SAMPLE[args.workload]
         procs = min(CPU_PROCS.get(args.workload, 1), os.cpu_count() or 1, nc)
         line["cpu_baseline"] = cpu_sample(args.workload, nc if procs > 1 else min(nc, 4), nt, procs)
-        line["grid_error"] = grid_error_sample(args.workload, dev, plan, inter)
+        line["grid_error"] = grid_error_sample(args.workload, dev, plan, inter, stack_k)
     return line
 
 
@@ -691,9 +728,15 @@ def _oracle_setup(workload, chans, n_times):
     """Inputs (one channel each) and the oracle's table for the CPU sample (untimed)."""
     import oracle
     import synth
-    sets = [synth.make(workload, n_chan=1, chan0=c, n_times=n_times) for c in chans]
+    base, _ = SYNTH_NAME.get(workload, (workload, {}))
+    sets = [synth.make(base, n_chan=1, chan0=c, n_times=n_times) for c in chans]
     wl = sets[0]
-    ot = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+    if WSTACK.get(workload):
+        from oracle.wstack import stacking_table
+        K = WSTACK[workload]
+        ot = stacking_table(wl.du, K, wl.w_max, wl.oversample, wl.taper_support, supports=[WSTACK_SUPPORT] * K)
+    else:
+        ot = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
     return sets, ot
 
 
@@ -708,7 +751,11 @@ def _oracle_run(workload, wl, ot):
     inter = INTERLEAVE.get(workload, False)
     t0 = time.perf_counter()
     pl = oracle.place(wl.uvw, wl.freq, wl.du, wl.n_grid, ot, flag=f)
-    if COMPRESS[workload] and inter:
+    if WSTACK.get(workload):
+        from oracle.wstack import grid_stacked
+        g, c = oracle.classify(pl)
+        grid_stacked(pl, ot, vis, w, f, wl.n_grid)
+    elif COMPRESS[workload] and inter:
         g, c, *_ = compress(pl, vis, w, f, interleave=True)
         oracle.grid_compressed(pl, ot, vis, w, f, wl.n_grid, interleave=True)
     elif COMPRESS[workload]:
@@ -781,7 +828,7 @@ def cpu_sample(workload, n_chan, n_times, procs=1):
                           workload, n_chan, n_times, res[0][3], sum(r[4] for r in res), procs)}
 
 
-def grid_error_sample(workload, dev, plan, interleave=False):
+def grid_error_sample(workload, dev, plan, interleave=False, stack_k=0):
     """Grid error of the CUDA path against the FP64 oracle (plain definition, eq. "gridding") on a
     seeded slice of the workload (300 baselines x 24 steps x 2 channels), with the bench's plan."""
     import numpy as np
@@ -790,20 +837,31 @@ def grid_error_sample(workload, dev, plan, interleave=False):
     import oracle
     import paper_1403_4209_gb300 as wg
     import synth
-    wl = synth.make(workload, n_chan=2, n_times=24, n_baselines=300)
-    tab = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
-    g = wg.Grid(wl.n_grid, wl.du, wl.n_pol, 1 if interleave else wl.n_chan, device=dev)
+    base, kw = SYNTH_NAME.get(workload, (workload, {}))
+    wl = synth.make(base, n_chan=2, n_times=24, n_baselines=300)
+    if stack_k:
+        sup = [WSTACK_SUPPORT] * stack_k
+        tab = wg.ConvTable.build(wl.du, stack_k, wl.w_max, wl.oversample, wl.taper_support, supports=sup, stacking=True)
+    else:
+        tab = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+    g = wg.Grid(wl.n_grid, wl.du, wl.n_pol, 1 if interleave else wl.n_chan * max(1, stack_k), device=dev)
     b = wg.VisBatch(torch.as_tensor(wl.uvw, device=dev), torch.as_tensor(wl.freq, device=dev), wl.vis.to(dev),
                     wl.weight.to(dev), wl.flag.to(dev))
     w = wg.WorkList(wl.rows * wl.n_chan, wl.n_chan, wl.n_pol)
-    wg.vis_compress(g, tab, b, w, compress=COMPRESS[workload], interleave=interleave)
+    wg.vis_compress(g, tab, b, w, compress=COMPRESS[workload], interleave=interleave, wstack=bool(stack_k))
     w.plan(tab, *plan)
     wg.grid_vis(g, tab, w)
     got = g.data.cpu().numpy()
-    ot = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
     f = wl.flag.numpy()
-    pl = oracle.place(wl.uvw, wl.freq, wl.du, wl.n_grid, ot, flag=f)
-    ref = oracle.grid_plain(pl, ot, wl.vis.numpy(), wl.weight.numpy(), f, wl.n_grid, interleave=interleave)
+    if stack_k:
+        from oracle.wstack import grid_stacked, stacking_table
+        ot = stacking_table(wl.du, stack_k, wl.w_max, wl.oversample, wl.taper_support, supports=sup)
+        pl = oracle.place(wl.uvw, wl.freq, wl.du, wl.n_grid, ot, flag=f)
+        ref = grid_stacked(pl, ot, wl.vis.numpy(), wl.weight.numpy(), f, wl.n_grid)
+    else:
+        ot = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+        pl = oracle.place(wl.uvw, wl.freq, wl.du, wl.n_grid, ot, flag=f)
+        ref = oracle.grid_plain(pl, ot, wl.vis.numpy(), wl.weight.numpy(), f, wl.n_grid, interleave=interleave)
     return {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
             "max_abs_over_max": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
             "reference": "FP64 oracle, plain gridding definition",

@@ -300,7 +300,7 @@ def grid_autotune(grid: Grid, table: ConvTable, worklist: WorkList, candidates=N
 
 
 def vis_weight(grid: Grid, table: ConvTable, batch: VisBatch, scheme: str = "uniform", robust: float = 0.0,
-               interleave: bool = False, out: torch.Tensor = None, stream=None) -> torch.Tensor:
+               interleave: bool = False, wstack: bool = False, out: torch.Tensor = None, stream=None) -> torch.Tensor:
     """Uniform or robust (Briggs) weights for the batch from the density of its griddable records
     per grid cell (WG_WEIGHT_UNIFORM / WG_WEIGHT_ROBUST); returns float32 [rows][chan][pol]."""
     codes = {"uniform": CONST["WG_WEIGHT_UNIFORM"], "robust": CONST["WG_WEIGHT_ROBUST"]}
@@ -309,7 +309,8 @@ def vis_weight(grid: Grid, table: ConvTable, batch: VisBatch, scheme: str = "uni
     if out.dtype != torch.float32 or out.shape != batch.weight.shape or not out.is_contiguous():
         raise ValueError("out must be a contiguous float32 tensor shaped like the weights")
     check(lib.vis_weight(grid.handle, table.handle, ctypes.byref(batch.struct), codes[scheme], float(robust),
-                         PREP_INTERLEAVE if interleave else 0, c_vp(out.data_ptr()), _stream(stream)), "vis_weight")
+                         (PREP_INTERLEAVE if interleave else 0) | (PREP_WSTACK if wstack else 0),
+                         c_vp(out.data_ptr()), _stream(stream)), "vis_weight")
     return out
 
 
