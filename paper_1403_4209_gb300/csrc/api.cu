@@ -108,6 +108,7 @@ int grid_destroy(wg_grid* h)
     cudaFree(g.icorr);
     cudaFree(g.inv_norm);
     if (g.plan_ok) cufftDestroy(g.plan);
+    if (g.plan_c_ok) cufftDestroy(g.plan_c);
     delete h;
     return WG_OK;
 }
@@ -245,7 +246,7 @@ int worklist_destroy(wg_worklist* h)
 {
     if (!h) return WG_OK;
     WorkList& w = h->w;
-    void* ptrs[] = {w.rinfo, w.rclass, w.tile_cnt, w.entries, w.gamma, w.runs, w.seg_nblk, w.seg_off,
+    void* ptrs[] = {w.rinfo, w.rclass, w.tile_cnt, w.carry_q, w.carry_last, w.entries, w.gamma, w.runs, w.seg_nblk, w.seg_off,
                     w.scal, w.chan_base, w.norm_priv, w.norm_batch, w.stat_priv, w.stats, w.task_counter};
     for (void* p : ptrs) cudaFree(p);
     delete h;
@@ -281,6 +282,8 @@ int worklist_create(int64_t max_records, int32_t C, int32_t P, wg_worklist** out
     al((void**)&w.rinfo, sizeof(int4) * max_records);
     al((void**)&w.rclass, max_records);
     al((void**)&w.tile_cnt, sizeof(int) * w.tile_cap);
+    al((void**)&w.carry_q, sizeof(float2) * w.tile_cap * P);
+    al((void**)&w.carry_last, sizeof(int) * w.tile_cap);
     al((void**)&w.entries, sizeof(int4) * max_records);
     al((void**)&w.gamma, sizeof(float2) * max_records * P);
     al((void**)&w.runs, sizeof(int2) * max_records);

@@ -1,7 +1,8 @@
 // Image finaliser (thesis Sec. 4.7, Algorithm "finalizer") for one grid:
-//   1. inverse FFT of each polarised grid: cuFFT C2C (FP32), one call per polarisation over a
-//      group of channels (stride P, distance N^2 P), groups sized to a 1 GiB scratch; Stokes I
-//      transforms only the parallel hands.  Centring (u = 0 at N/2 -> l = 0 at N/2) uses the
+//   1. inverse FFT of each polarised grid: cuFFT C2C (FP32) over contiguous N x N planes; the
+//      needed polarisations of a group of channels (groups sized to a 1 GiB scratch) are first
+//      split out of the pixel-interleaved grid, so Stokes I copies and transforms only the
+//      parallel hands.  Centring (u = 0 at N/2 -> l = 0 at N/2) uses the
 //      (-1)^(x+y) modulation before and (-1)^(mx+my) after the transform (N even);
 //   2. real part, divided by the normaliser N_p (eq. "normalizer"); Stokes I as the mean of
 //      polarisations 0 and P-1;
@@ -53,9 +54,29 @@ __global__ void k_modulate(const float2* __restrict__ src, float2* __restrict__ 
     dst[idx] = v;
 }
 
-// one thread per pixel of a group of G channels
-__global__ void k_finish(const float2* __restrict__ f, int N, int P, int64_t npix, const float* __restrict__ icorr,
-                         const float* __restrict__ inv_norm, int mode, float* __restrict__ img)
+// step 1 input for a group of G channels: the needed polarisations (np of them, listed in pols)
+// of each pixel, times (-1)^(x+y), into contiguous planes f[pi][gch][N][N] for unit-stride FFTs
+__global__ void k_split(const float2* __restrict__ grid, float2* __restrict__ f, int N, int P, int G, int np,
+                        int4 pols)
+{
+    const int64_t nn = (int64_t)N * N;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;     // over G x N x N pixels
+    if (q >= (int64_t)G * nn) return;
+    const int64_t gch = q / nn, pix = q - gch * nn;
+    const int y = (int)(pix / N), x = (int)(pix - (int64_t)y * N);
+    const float sg = ((x + y) & 1) ? -1.f : 1.f;
+    const float2* src = grid + q * P;
+    const int pl[4] = {pols.x, pols.y, pols.z, pols.w};
+    for (int pi = 0; pi < np; ++pi) {
+        const float2 v = src[pl[pi]];
+        f[((int64_t)pi * G + gch) * nn + pix] = make_float2(sg * v.x, sg * v.y);
+    }
+}
+
+// steps 2-4 from the planes of k_split after their inverse FFTs (one thread per pixel of the group)
+__global__ void k_finish_planes(const float2* __restrict__ f, int N, int P, int G, int64_t npix,
+                                const float* __restrict__ icorr, const float* __restrict__ inv_norm, int mode,
+                                float* __restrict__ img)
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= npix) return;
@@ -63,37 +84,42 @@ __global__ void k_finish(const float2* __restrict__ f, int N, int P, int64_t npi
     const int64_t gch = q / nn, pix = q - gch * nn;
     const int my = (int)(pix / N), mx = (int)(pix - (int64_t)my * N);
     const float cc = ((mx + my) & 1 ? -1.f : 1.f) * icorr[mx] * icorr[my];
-    const float2* fp = f + q * P;
     const float* in = inv_norm ? inv_norm + gch * P : nullptr;
+    auto plane = [&](int pi) { return f[((int64_t)pi * G + gch) * nn + pix]; };
+    if (mode == WG_IMAGE_STOKES_I) {
+        const float v0 = plane(0).x * in[0] * cc;
+        img[gch * nn + pix] = (P == 1) ? v0 : 0.5f * (v0 + plane(1).x * in[P - 1] * cc);
+        return;
+    }
     if (mode == WG_IMAGE_PER_POL || mode == WG_IMAGE_PER_POL_RAW) {
-        for (int p = 0; p < P; ++p) img[(gch * P + p) * nn + pix] = fp[p].x * (in ? in[p] : 1.f) * cc;
-    } else if (mode == WG_IMAGE_STOKES_LINEAR || mode == WG_IMAGE_STOKES_CIRCULAR) {
-        // Stokes from the complex per-polarisation images z_p = f_p / N_p (step 2)
-        float2 z[4];
-        for (int p = 0; p < P; ++p) z[p] = make_float2(fp[p].x * in[p] * cc, fp[p].y * in[p] * cc);
-        float* o = img + (gch * P) * nn + pix;
-        if (P == 1) {
-            o[0] = z[0].x;
-        } else if (P == 2) {
-            o[0] = 0.5f * (z[0].x + z[1].x);
-            o[nn] = 0.5f * (z[0].x - z[1].x);
-        } else {
-            const float par_s = 0.5f * (z[0].x + z[3].x), par_d = 0.5f * (z[0].x - z[3].x);
-            const float crs_s = 0.5f * (z[1].x + z[2].x), crs_d = 0.5f * (z[1].y - z[2].y);   // Re(-j(z1 - z2))/2
-            o[0] = par_s;                                                                      // I
-            if (mode == WG_IMAGE_STOKES_LINEAR) {
-                o[nn] = par_d;            // Q = (XX - YY)/2
-                o[2 * nn] = crs_s;        // U = (XY + YX)/2
-                o[3 * nn] = crs_d;        // V = -j (XY - YX)/2
-            } else {
-                o[nn] = crs_s;            // Q = (RL + LR)/2
-                o[2 * nn] = crs_d;        // U = -j (RL - LR)/2
-                o[3 * nn] = par_d;        // V = (RR - LL)/2
-            }
-        }
+        for (int p = 0; p < P; ++p) img[(gch * P + p) * nn + pix] = plane(p).x * (in ? in[p] : 1.f) * cc;
+        return;
+    }
+    // Stokes from the complex per-polarisation images z_p = f_p / N_p (step 2)
+    float2 z[4];
+    for (int p = 0; p < P; ++p) {
+        const float2 v = plane(p);
+        z[p] = make_float2(v.x * in[p] * cc, v.y * in[p] * cc);
+    }
+    float* o = img + (gch * P) * nn + pix;
+    if (P == 1) {
+        o[0] = z[0].x;
+    } else if (P == 2) {
+        o[0] = 0.5f * (z[0].x + z[1].x);
+        o[nn] = 0.5f * (z[0].x - z[1].x);
     } else {
-        const float v0 = fp[0].x * in[0] * cc;
-        img[gch * nn + pix] = (P == 1) ? v0 : 0.5f * (v0 + fp[P - 1].x * in[P - 1] * cc);
+        const float par_s = 0.5f * (z[0].x + z[3].x), par_d = 0.5f * (z[0].x - z[3].x);
+        const float crs_s = 0.5f * (z[1].x + z[2].x), crs_d = 0.5f * (z[1].y - z[2].y);   // Re(-j(z1 - z2))/2
+        o[0] = par_s;                                                                      // I
+        if (mode == WG_IMAGE_STOKES_LINEAR) {
+            o[nn] = par_d;            // Q = (XX - YY)/2
+            o[2 * nn] = crs_s;        // U = (XY + YX)/2
+            o[3 * nn] = crs_d;        // V = -j (XY - YX)/2
+        } else {
+            o[nn] = crs_s;            // Q = (RL + LR)/2
+            o[2 * nn] = crs_d;        // U = -j (RL - LR)/2
+            o[3 * nn] = par_d;        // V = (RR - LL)/2
+        }
     }
 }
 
@@ -254,18 +280,32 @@ int launch_correct(Grid& g, const Table& t, int mode, float* image, cudaStream_t
         k_inv_norm<<<(C * P + 127) / 128, 128, 0, s>>>(g.norm, C * P, g.inv_norm);
         WG_LAUNCHED("k_inv_norm");
     }
+    if (!g.plan_c_ok) {
+        int n[2] = {N, N};
+        if (cufftPlanMany(&g.plan_c, 2, n, nullptr, 1, N * N, nullptr, 1, N * N, CUFFT_C2C, G) != CUFFT_SUCCESS)
+            return fail(WG_E_CUDA, "cufftPlanMany(%d x %d, contiguous, batch %d) failed", N, N, G);
+        g.plan_c_ok = true;
+    }
+    if (cufftSetStream(g.plan_c, s) != CUFFT_SUCCESS) return fail(WG_E_CUDA, "cufftSetStream failed");
+    // the polarisations the mode needs: Stokes I only the parallel hands
+    int np = P;
+    int4 pols = make_int4(0, 1, 2, 3);
+    if (mode == WG_IMAGE_STOKES_I) {
+        np = (P == 1) ? 1 : 2;
+        pols = make_int4(0, P - 1, 0, 0);
+    }
     const size_t img_stride = (mode == WG_IMAGE_STOKES_I) ? (size_t)N * N : (size_t)P * N * N;
     for (int c0 = 0; c0 < C; c0 += G) {
-        k_modulate<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g.data + (size_t)c0 * per_chan, g.scratch, N, P, tot);
-        WG_LAUNCHED("k_modulate");
-        for (int p = 0; p < P; ++p) {
-            if (mode == WG_IMAGE_STOKES_I && p != 0 && p != P - 1) continue;   // cross hands unused
-            cufftComplex* d = reinterpret_cast<cufftComplex*>(g.scratch + p);
-            if (cufftExecC2C(g.plan, d, d, CUFFT_INVERSE) != CUFFT_SUCCESS) return fail(WG_E_CUDA, "cufftExecC2C failed");
+        k_split<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(g.data + (size_t)c0 * per_chan, g.scratch, N, P, G, np,
+                                                               pols);
+        WG_LAUNCHED("k_split");
+        for (int pi = 0; pi < np; ++pi) {
+            cufftComplex* d = reinterpret_cast<cufftComplex*>(g.scratch + (size_t)pi * G * N * N);
+            if (cufftExecC2C(g.plan_c, d, d, CUFFT_INVERSE) != CUFFT_SUCCESS) return fail(WG_E_CUDA, "cufftExecC2C failed");
         }
-        k_finish<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(g.scratch, N, P, npix, g.icorr,
-                                                                raw ? nullptr : g.inv_norm + (size_t)c0 * P, mode,
-                                                                image + (size_t)c0 * img_stride);
+        k_finish_planes<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(g.scratch, N, P, G, npix, g.icorr,
+                                                                       raw ? nullptr : g.inv_norm + (size_t)c0 * P, mode,
+                                                                       image + (size_t)c0 * img_stride);
         WG_LAUNCHED("k_finish");
     }
     return WG_OK;

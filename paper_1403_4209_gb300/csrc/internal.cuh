@@ -68,6 +68,8 @@ struct Grid {
     float* inv_norm = nullptr;            // [n_chan][n_pol] 1 / N_p (0 where N_p = 0)
     int corr_s0 = -1, corr_beta = -1;
     cufftHandle plan = 0;
+    cufftHandle plan_c = 0;               // batch of scratch_chans contiguous N x N planes
+    bool plan_c_ok = false;
     bool plan_ok = false;
 };
 
@@ -106,6 +108,8 @@ struct WorkList {
     uint8_t* rclass = nullptr;
     // per (tile, chan)
     int* tile_cnt = nullptr;
+    float2* carry_q = nullptr;            // [tile_cap][P] run parts carried into a tile
+    int* carry_last = nullptr;            // [tile_cap] their last row (record), or -1
     // per gridded entry (channel-major)
     int4* entries = nullptr;
     float2* gamma = nullptr;

@@ -110,6 +110,8 @@ extern "C" int grid_vis_noalloc(const wg_grid_view* view, const wg_table* th, co
     w.rinfo = cv.take<int4>(cap);
     w.rclass = cv.take<uint8_t>(cap);
     w.tile_cnt = cv.take<int>(w.tile_cap);
+    w.carry_q = cv.take<float2>(w.tile_cap * P);
+    w.carry_last = cv.take<int>(w.tile_cap);
     w.entries = cv.take<int4>(cap);
     w.gamma = cv.take<float2>(cap * P);
     w.runs = cv.take<int2>(cap);

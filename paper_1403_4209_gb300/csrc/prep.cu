@@ -11,7 +11,8 @@
 //               channel bases, so gridded records land channel-major, row-ordered.
 //   k_compact   (Compress Index Generate + Compress and Weigh Visibilities, Algorithm
 //               "compressindex", eqs. "compress1"/"conjugatetake"): each gridded record
-//               walks its run of compressed successors and sums eps (1-f) psi-conj(vis); the
+//               walks its run of compressed successors and sums eps (1-f) psi-conj(vis) (a run
+//               crossing a tile end is finished by k_carry from the next tiles' carries); the
 //               run's eps (1-f) times its sub-kernel's zeta gives the normaliser terms (eq.
 //               "normalizer"), summed by k_norm_sum.
 //   k_segments + k_seg_scan (Plan Create / Plan Analyse, Algorithm "plan"): gridded entries
@@ -493,7 +494,8 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
                                                  const int* __restrict__ chan_base, PlaceParams pp,
                                                  int4* __restrict__ entries, float2* __restrict__ gamma,
                                                  int2* __restrict__ runs, int64_t cap_entries,
-                                                 double* __restrict__ norm_priv, long long* __restrict__ scal, int vec)
+                                                 double* __restrict__ norm_priv, float2* __restrict__ carry_q,
+                                                 int* __restrict__ carry_last, long long* __restrict__ scal, int vec)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int64_t tile = blockIdx.x;
@@ -541,20 +543,24 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
     }
     __syncthreads();
 
+    // pass 2: work items are the tile's gridded records (runs summed inside the tile) and, per
+    // sequence (channel; the one natural-order sequence when interleaved), the compressed
+    // records the tile starts with, which continue a run of an earlier tile: their sum is left
+    // in carry[tile][sequence] for k_carry to add to that run's entry.
     const int nh = n_heads;
-    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
-        const int j = s_heads[h];
+    const int n_seq = IL ? 1 : C;
+    const int stride = IL ? 1 : C;
+    for (int h = threadIdx.x; h < nh + n_seq; h += blockDim.x) {
+        const bool is_carry = h >= nh;
+        const int j = is_carry ? h - nh : s_heads[h];          // a carry starts at the sequence's first record
         const int rr = j / C, ch = j - rr * C;
         const int64_t row = row0 + rr, rec = row * C + ch;
-        const int gch = IL ? 0 : ch;       // the work-list list (and normaliser row)
-        const int4 info = rinfo[rec];
-        const int ech = pp.wstack ? ch * pp.K + (info.w & 0xFFF) : gch;   // the grid channel
-        const int rank = (info.w >> 16) & 0xFFFF;
-        const int dst = chan_base[gch] + tile_off[tile * C + gch] + rank;
-        if (dst < 0 || (int64_t)dst >= cap_entries) {   // cannot happen with a consistent scan
-            atomicAdd(reinterpret_cast<unsigned long long*>(&scal[3]), 1ull);
+        const int gch = IL ? 0 : ch;                           // the work-list list (and normaliser row)
+        if (is_carry && !(s_cls[j] & 2)) {                     // no run continues into this tile
+            carry_last[tile * C + gch] = -1;
             continue;
         }
+        const int4 info = rinfo[rec];
         float2 acc[P];
         float wsum[P];
 #pragma unroll
@@ -562,14 +568,11 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
             acc[p] = s_q[(size_t)p * cap + j];
             wsum[p] = s_w[(size_t)p * cap + j];
         }
-        // the run: the successors (next rows of the channel; interleaved: next records) while
-        // they are compressed, first in this tile, then in the next tiles.  `last` is the run's
-        // last row (interleaved: last record).  The two orders keep separate loops.
-        int64_t last;
+        // the run inside the tile: successors (next rows of the channel, or next records when
+        // interleaved) while compressed; `last` is its last row (interleaved: record)
+        int64_t last = IL ? rec : row;
         if constexpr (!IL) {
-            last = row;
-            int r2 = rr + 1;
-            for (; r2 < nrows; ++r2) {
+            for (int r2 = rr + 1; r2 < nrows; ++r2) {
                 const int j2 = r2 * C + ch;
                 if (!(s_cls[j2] & 2)) break;
 #pragma unroll
@@ -581,28 +584,8 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
                 }
                 last = row0 + r2;
             }
-            if (r2 == nrows) {
-                const float scale = vis_scale ? vis_scale[ch] : 1.0f;
-                for (int64_t g2 = row0 + nrows; g2 < rows; ++g2) {
-                    const int64_t rc2 = g2 * C + ch;
-                    const int cls2 = rclass[rc2];
-                    if (!(cls2 & 2)) break;
-#pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        float wf;
-                        const float2 q = weighted(vis, weight, flag, rc2 * P + src_pol(p, (cls2 >> 3) & 1, pp.cross_swap),
-                                                  scale, (cls2 >> 3) & 1, unweighted, wf);
-                        acc[p].x += q.x;
-                        acc[p].y += q.y;
-                        wsum[p] += wf;
-                    }
-                    last = g2;
-                }
-            }
         } else {
-            last = rec;
-            int j2 = j + 1;
-            for (; j2 < nrec; ++j2) {
+            for (int j2 = j + 1; j2 < nrec; ++j2) {
                 if (!(s_cls[j2] & 2)) break;
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
@@ -613,44 +596,67 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
                 }
                 last = row0 * C + j2;
             }
-            if (j2 == nrec) {
-                int c2 = 0;                                // channel of the record rc2
-                const int64_t n_all = rows * C;
-                for (int64_t rc2 = (row0 + nrows) * C; rc2 < n_all; ++rc2) {
-                    const int cls2 = rclass[rc2];
-                    if (!(cls2 & 2)) break;
-                    const float scale = vis_scale ? vis_scale[c2] : 1.0f;
-#pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        float wf;
-                        const float2 q = weighted(vis, weight, flag, rc2 * P + src_pol(p, (cls2 >> 3) & 1, pp.cross_swap),
-                                                  scale, (cls2 >> 3) & 1, unweighted, wf);
-                        acc[p].x += q.x;
-                        acc[p].y += q.y;
-                        wsum[p] += wf;
-                    }
-                    last = rc2;
-                    c2 = (c2 + 1 == C) ? 0 : c2 + 1;
-                }
-            }
         }
+        (void)stride;
         const int k = info.w & 0xFFF;
-        entries[dst] = make_int4(info.x, info.y, info.z, k | (ech << 16));
-#pragma unroll
-        for (int p = 0; p < P; ++p) gamma[(int64_t)dst * P + p] = acc[p];
-        // runs: first and last row of the channel, or first and last record when interleaved
-        runs[dst] = make_int2(IL ? (int)rec : (int)row, (int)last);
         const int S = __ldg(&pp.supports[k]);
         const int sub = (info.z - __ldg(&pp.offsets[k])) / (S * S);
         const float zeta = __ldg(&pp.zeta_f[k * pp.beta * pp.beta + sub]);
 #pragma unroll
         for (int p = 0; p < P; ++p)
             if (wsum[p] != 0.f) atomicAdd(&s_norm[gch * P + p], zeta * wsum[p]);
+        if (is_carry) {
+            const int64_t c = tile * C + gch;
+#pragma unroll
+            for (int p = 0; p < P; ++p) carry_q[c * P + p] = acc[p];
+            carry_last[c] = (int)last;
+            continue;
+        }
+        const int rank = (info.w >> 16) & 0xFFFF;
+        const int dst = chan_base[gch] + tile_off[tile * C + gch] + rank;
+        if (dst < 0 || (int64_t)dst >= cap_entries) {   // cannot happen with a consistent scan
+            atomicAdd(reinterpret_cast<unsigned long long*>(&scal[3]), 1ull);
+            continue;
+        }
+        const int ech = pp.wstack ? ch * pp.K + k : gch;   // the grid channel
+        entries[dst] = make_int4(info.x, info.y, info.z, k | (ech << 16));
+#pragma unroll
+        for (int p = 0; p < P; ++p) gamma[(int64_t)dst * P + p] = acc[p];
+        // runs: first and last row of the channel, or first and last record when interleaved
+        runs[dst] = make_int2(IL ? (int)rec : (int)row, (int)last);
     }
     __syncthreads();
     const int slot = (int)(tile % kNormSlots);
     for (int i = threadIdx.x; i < C * P; i += blockDim.x)
         if (s_norm[i] != 0.f) atomicAdd(&norm_priv[(int64_t)slot * C * P + i], (double)s_norm[i]);
+}
+
+// adds each tile's carried run part (compressed records continuing a run of an earlier tile) to
+// that run's entry, the last entry of the sequence before the tile, and extends the run's end
+template <int P>
+__global__ void k_carry(const float2* __restrict__ carry_q, const int* __restrict__ carry_last, int64_t n_tiles, int C,
+                        int n_seq, const int* __restrict__ tile_off, const int* __restrict__ chan_base,
+                        float2* __restrict__ gamma, int2* __restrict__ runs, int64_t cap_entries,
+                        long long* __restrict__ scal)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // tile * C + sequence
+    if (c >= n_tiles * C) return;
+    const int seq = (int)(c % C);
+    if (seq >= n_seq) return;                            // interleaved: one sequence per tile
+    const int last = carry_last[c];
+    if (last < 0) return;
+    const int64_t dst = (int64_t)chan_base[seq] + tile_off[c] - 1;
+    if (dst < chan_base[seq] || dst >= cap_entries) {   // cannot happen: a compressed record follows its run's head
+        atomicAdd(reinterpret_cast<unsigned long long*>(&scal[3]), 1ull);
+        return;
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const float2 q = carry_q[c * P + p];
+        atomicAdd(&gamma[dst * P + p].x, q.x);
+        atomicAdd(&gamma[dst * P + p].y, q.y);
+    }
+    atomicMax(reinterpret_cast<int*>(&runs[dst]) + 1, last);
 }
 
 // N_p of the batch: the sum of the privatised per-slot partials
@@ -819,8 +825,8 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
             k_compact<P, VT, IL><<<(unsigned)n_tiles, 512, sm, s>>>(
                 wl.rinfo, wl.rclass, reinterpret_cast<const VT*>(in.vis),
                 std::is_same<VT, float2>::value ? nullptr : in.vis_scale, in.weight, in.flag, rows, rpb,
-                C, wl.tile_cnt, wl.chan_base, pp, wl.entries, wl.gamma, wl.runs, wl.cap, wl.norm_priv, wl.scal,
-                std::is_same<VT, float2>::value ? vec : 0);
+                C, wl.tile_cnt, wl.chan_base, pp, wl.entries, wl.gamma, wl.runs, wl.cap, wl.norm_priv, wl.carry_q,
+                wl.carry_last, wl.scal, std::is_same<VT, float2>::value ? vec : 0);
             return WG_OK;
         };
         int rc;
@@ -830,6 +836,13 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
             rc = pp.interleave ? launch(float2{}, std::true_type{}) : launch(float2{}, std::false_type{});
         if (rc != WG_OK) return rc;
         WG_LAUNCHED("k_compact");
+    }
+    if (rows > 0) {
+        const int64_t nc = n_tiles * C;
+        k_carry<P><<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(wl.carry_q, wl.carry_last, n_tiles, C,
+                                                                 pp.interleave ? 1 : C, wl.tile_cnt, wl.chan_base,
+                                                                 wl.gamma, wl.runs, wl.cap, wl.scal);
+        WG_LAUNCHED("k_carry");
     }
     k_norm_sum<<<1, 256, 0, s>>>(wl.norm_priv, C * P, wl.norm_batch);
     WG_LAUNCHED("k_norm_sum");
