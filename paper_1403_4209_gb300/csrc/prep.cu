@@ -31,6 +31,44 @@ namespace wg {
 
 namespace {
 
+// a mod S for 0 <= a < 2^20 and 1 <= S < 2^12: the float quotient a (1/S) is within one of the
+// integer one, and one correction step each way makes the remainder exact
+__device__ __forceinline__ int mod_small(int a, int S, float inv_s)
+{
+    const int q = __float2int_rz((float)a * inv_s);
+    int r = a - q * S;
+    r += (r < 0) ? S : 0;
+    r -= (r >= S) ? S : 0;
+    return r;
+}
+
+// (j / C, j % C) for 0 <= j < 2^20 and 1 <= C < 2^12, by the corrected float quotient
+__device__ __forceinline__ int2 divmod_small(int j, int C, float inv_c)
+{
+    int q = __float2int_rz((float)j * inv_c);
+    int r = j - q * C;
+    if (r < 0) { --q; r += C; }
+    if (r >= C) { ++q; r -= C; }
+    return make_int2(q, r);
+}
+
+// some polarisation of record rec unflagged; with `vec` (flag pointer aligned to P bytes) the P
+// flag bytes are read in one load and tested for a zero byte
+__device__ __forceinline__ bool any_unflagged(const uint8_t* __restrict__ flag, int64_t rec, int P, int vec)
+{
+    if (vec && P == 4) {
+        const unsigned w = __ldg(reinterpret_cast<const unsigned*>(flag) + rec);
+        return ((w - 0x01010101u) & ~w & 0x80808080u) != 0;     // a zero byte
+    }
+    if (vec && P == 2) {
+        const unsigned short f = __ldg(reinterpret_cast<const unsigned short*>(flag) + rec);
+        return (f & 0xFF) == 0 || (f >> 8) == 0;
+    }
+    bool any = false;
+    for (int p = 0; p < P; ++p) any |= (__ldg(flag + rec * P + p) == 0);
+    return any;
+}
+
 // floor(a / d) for d > 0; a shift when d = 2^sh (sh >= 1)
 __device__ __forceinline__ int floor_div32(int a, int d, int sh)
 {
@@ -165,11 +203,12 @@ __device__ __forceinline__ Placed place(const double* __restrict__ uvw, int64_t 
     const int h = (S - 1) / 2;
     const int x0 = pp.N / 2 + xc - h, y0 = pp.N / 2 + yc - h;
     if (x0 < 0 || y0 < 0 || x0 + S - 1 > pp.N - 1 || y0 + S - 1 > pp.N - 1) return o;
-    bool unflagged = false;
-    for (int p = 0; p < P; ++p) unflagged |= (flag[rec * P + p] == 0);
-    if (!unflagged) return o;
+    if (!any_unflagged(flag, rec, P, pp.flag_vec)) return o;
     const int sub = (fv - pp.lo) * pp.beta + (fu - pp.lo);
-    const int cu = (S - x0 % S) % S, cv = (S - y0 % S) % S;
+    // (-x0) mod S: the residue class of the footprint's first column (x0 >= 0)
+    const float inv_s = __frcp_rn((float)S);
+    const int rx = mod_small(x0, S, inv_s), ry = mod_small(y0, S, inv_s);
+    const int cu = rx ? S - rx : 0, cv = ry ? S - ry : 0;
     o.info.x = x0 | (y0 << 16);
     o.info.y = cu | (cv << 16);
     o.info.z = __ldg(&pp.offsets[k]) + sub * S * S;
@@ -246,6 +285,7 @@ __global__ void __launch_bounds__(512, 3) k_classify(const double* __restrict__ 
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int C = pp.C;
+    const float inv_c = __frcp_rn((float)C);
     const int64_t tile = blockIdx.x;
     const int64_t row0 = tile * rpb;
     const int nrows = (int)min((int64_t)rpb, rows - row0);
@@ -267,16 +307,19 @@ __global__ void __launch_bounds__(512, 3) k_classify(const double* __restrict__ 
 
     // pass 1: placement
     for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
-        const int rr = j / C, ch = j - rr * C;
+        const int2 qr = divmod_small(j, C, inv_c);
+        const int rr = qr.x, ch = qr.y;
         const int64_t row = row0 + rr, rec = row * C + ch;
         s_info[j] = place(uvw, row, s_row[rr + 1], lam_inv[ch], sc[ch], lam_f[ch], sc_f[ch], flag, rec, P, pp).info;
     }
     __syncthreads();
 
     // pass 2: compression indicator, g, statistics
-    unsigned long long n_gd = 0, n_g = 0, n_c = 0, u_g = 0, u_c = 0;
+    // per thread at most cap / blockDim records, so the counts fit 32 bits, and so do warp sums
+    unsigned n_gd = 0, n_g = 0, n_c = 0, u_g = 0, u_c = 0;
     for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
-        const int rr = j / C, ch = j - rr * C;
+        const int2 qr = divmod_small(j, C, inv_c);
+        const int rr = qr.x, ch = qr.y;
         const int64_t row = row0 + rr, rec = row * C + ch;
         const int4 info = s_info[j];
         const int gd = (info.w >> kBitGd) & 1;
@@ -300,22 +343,21 @@ __global__ void __launch_bounds__(512, 3) k_classify(const double* __restrict__ 
         s_gc[j] = (unsigned char)(g | (c << 1) | (gd << 2) | (((info.w >> kBitNeg) & 1) << 3));
         s_scan[pp.interleave ? j : ch * nrows + rr] = g;
         if (gd) {
-            const unsigned long long S = (unsigned long long)__ldg(&pp.supports[info.w & 0xFFF]);
+            const unsigned S = (unsigned)__ldg(&pp.supports[info.w & 0xFFF]);
             n_gd += 1;
             n_g += g;
             n_c += c;
-            u_g += g ? S * S : 0ull;
-            u_c += c ? S * S : 0ull;
+            u_g += g ? S * S : 0u;
+            u_c += c ? S * S : 0u;
         }
     }
     // block statistics
     {
-        unsigned long long v[5] = {n_gd, n_g, n_c, u_g, u_c};
+        const unsigned v[5] = {n_gd, n_g, n_c, u_g, u_c};
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-            unsigned long long x = v[q];
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_stat[q + 1], x);
+            const unsigned x = __reduce_add_sync(0xffffffffu, v[q]);
+            if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_stat[q + 1], (unsigned long long)x);
         }
     }
     __syncthreads();
@@ -325,7 +367,8 @@ __global__ void __launch_bounds__(512, 3) k_classify(const double* __restrict__ 
 
     // pass 4: outputs
     for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
-        const int rr = j / C, ch = j - rr * C;
+        const int2 qr = divmod_small(j, C, inv_c);
+        const int rr = qr.x, ch = qr.y;
         const int64_t rec = (row0 + rr) * C + ch;
         int4 info = s_info[j];
         const int gc = s_gc[j];
@@ -761,6 +804,7 @@ static PlaceParams place_params(const Table& t, int n, double du, int C, int P, 
     for (int b = 0; b < 16; ++b)
         if (t.beta == (1 << b)) pp.beta_log2 = b;
     pp.zeta_f = t.zeta_f;
+    pp.flag_vec = 0;
     return pp;
 }
 
@@ -783,6 +827,7 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
     wl.N = g.n;
 
     PlaceParams pp = place_params(t, g.n, g.du, C, P, flags);
+    pp.flag_vec = (reinterpret_cast<uintptr_t>(in.flag) % P) == 0;
     wl.interleave = pp.interleave != 0;
     wl.cross_swap = pp.cross_swap != 0;
     wl.wstack_k = pp.wstack ? t.K : 1;
@@ -981,6 +1026,7 @@ static int weight_impl(const Table& t, const Grid& g, const wg_vis_in& in, int s
     const int C = in.n_chan;
     const int64_t rows = in.n_rows;
     PlaceParams pp = place_params(t, g.n, g.du, C, P, flags);
+    pp.flag_vec = (reinterpret_cast<uintptr_t>(in.flag) % P) == 0;
     const int gc = pp.interleave ? 1 : C;
     const int64_t n_cells = (int64_t)gc * g.n * g.n;
     const size_t bytes = sizeof(float) * (size_t)n_cells * P + sizeof(double) * (4 * C + 2 * P);
