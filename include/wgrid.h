@@ -222,8 +222,9 @@ typedef struct wg_vis_in {
 /* ---- work list: the preparation phase's outputs (Sec. 4.3.4) ----------------------- */
 typedef struct wg_worklist wg_worklist;
 
-/* Allocates device buffers for up to max_records = n_rows * n_chan records.
- * Errors: INVALID_ARG, OOM. */
+/* Allocates device buffers for up to max_records = n_rows * n_chan records: about
+ * 41 + 16 n_pol bytes per record (placement, entries, weighted visibilities, runs and the
+ * degridder's per-entry sums).  Errors: INVALID_ARG, OOM. */
 int worklist_create(int64_t max_records, int32_t n_chan, int32_t n_pol, wg_worklist** out);
 int worklist_destroy(wg_worklist* wl);
 
@@ -348,6 +349,9 @@ int vis_weight(const wg_grid* grid, const wg_table* table, const wg_vis_in* in, 
 
 /* A7 (not in the thesis): for every input record, m_p = sum_ij conj(C_k[i][j]) grid_p(y0+i,
  * x0+j), conjugated back where psi = -1; WG_DEGRID_ADJOINT also multiplies by eps (1-f).
+ * Runs the gridder's tasks under the work list's plan (worklist_plan / grid_autotune): the
+ * sums are taken once per gridded entry into the work list's FP32 accumulator, then written
+ * to every record of the entry's run.
  * After a vis_compress with WG_PREP_CROSS_SWAP, pols 1 and 2 of a psi = -1 record come from
  * grid pols 2 and 1.  Records that are not griddable get 0.  `in` and `wl` must be the batch given to the
  * last vis_compress on `wl`.  vis_out: device complex64 [n_rows][n_chan][n_pol],

@@ -246,7 +246,7 @@ int worklist_destroy(wg_worklist* h)
 {
     if (!h) return WG_OK;
     WorkList& w = h->w;
-    void* ptrs[] = {w.rinfo, w.rclass, w.tile_cnt, w.carry_q, w.carry_last, w.entries, w.gamma, w.runs, w.seg_nblk, w.seg_off,
+    void* ptrs[] = {w.rinfo, w.rclass, w.tile_cnt, w.carry_q, w.carry_last, w.entries, w.gamma, w.runs, w.dacc, w.seg_nblk, w.seg_off,
                     w.scal, w.chan_base, w.norm_priv, w.norm_batch, w.stat_priv, w.stats, w.task_counter};
     for (void* p : ptrs) cudaFree(p);
     delete h;
@@ -287,6 +287,7 @@ int worklist_create(int64_t max_records, int32_t C, int32_t P, wg_worklist** out
     al((void**)&w.entries, sizeof(int4) * max_records);
     al((void**)&w.gamma, sizeof(float2) * max_records * P);
     al((void**)&w.runs, sizeof(int2) * max_records);
+    al((void**)&w.dacc, sizeof(float2) * max_records * P);
     al((void**)&w.seg_nblk, sizeof(int) * w.seg_cap);
     al((void**)&w.seg_off, sizeof(int) * (w.seg_cap + 1));
     al((void**)&w.scal, sizeof(long long) * 8);

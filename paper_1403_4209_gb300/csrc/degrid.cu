@@ -1,17 +1,33 @@
 // Degridding: the adjoint of the gridding map (not in the thesis).
 //
-// For a gridded entry (footprint origin (x0, y0), kernel pointer z, channel c) the kernel sum
+// For a gridded entry (footprint origin (x0, y0), kernel pointer z, grid channel c) the kernel sum
 //   m_p = sum_{i,j} conj(C[z + i S + j]) grid_c,p(y0 + i, x0 + j)
-// is a gather: one warp per entry (chunks of consecutive entries per warp), lanes striding over
-// the S x S footprint, a shuffle reduction.  Compression (Sec. 4.3.3) carries over: every record compressed into the entry
-// has the same footprint and kernel samples, so m is computed once per run and written to each
-// record of the run, conjugated back where psi = -1 (w' < 0), and for the adjoint mode scaled
+// takes two launches.
+//
+// k_degrid_sum runs the gridder's tasks (a segment of consecutive entries x one block of the
+// footprint, as the work list's plan defines them) with the gridder's ownership: each lane owns
+// R residue classes (x mod S, y mod S) of the footprint, so exactly one pixel of each class lies
+// in every entry's footprint (Romein's argument, Sec. 2.5).  The lane keeps those pixels' values
+// (all polarisations) in registers and reloads one only when the footprint moves and the class's
+// pixel changes; for consecutive entries of a track that keep the footprint and differ only in
+// the sub-kernel z it loads nothing but the kernel samples.  Per entry each lane sums its R
+// points, the warp reduces the 2P floats by a shuffle reduce-scatter, and 2P lanes add the
+// entry's sums into a per-entry FP32 accumulator (one atomic add per float per footprint block).
+//
+// k_degrid_out writes the records of each entry's run.  Compression (Sec. 4.3.3) carries over:
+// every record compressed into an entry has its footprint and kernel samples, so m is computed
+// once per entry and written to each record of the run, conjugated back where psi = -1 (w' < 0),
+// with the cross hands swapped back under cross-hand swapping, and for the adjoint mode scaled
 // by eps (1 - f) (the vis -> grid map's R-linear outer factor).
 #include "internal.cuh"
 
 namespace wg {
 
-typedef unsigned long long f32x2;     // a packed FP32 pair (Blackwell f32x2 arithmetic)
+namespace {
+
+constexpr int kWarps = 4;           // warps per block of k_degrid_sum
+
+typedef unsigned long long f32x2;   // a packed FP32 pair (Blackwell f32x2 arithmetic)
 
 __device__ __forceinline__ f32x2 pack2(float lo, float hi)
 {
@@ -34,7 +50,13 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
     return d;
 }
 
-// the P polarisations of one pixel as packed pairs
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
+
+// the P polarisations of one pixel as packed pairs (gx, gy)
 template <int P>
 __device__ __forceinline__ void load_pixel(const float2* __restrict__ g, f32x2 (&v)[P])
 {
@@ -50,129 +72,340 @@ __device__ __forceinline__ void load_pixel(const float2* __restrict__ g, f32x2 (
     }
 }
 
-constexpr int kDegridChunk = 4;     // consecutive entries a warp takes from the counter at a time
+// Per-warp shared memory: the residue-class arrays, then the segment's staged entries.
+struct WarpSmem {
+    int (*puv)[32];          // [kRMax][32] each lane's owned residue classes (pu | pv << 16)
+    int (*cur)[32];          // [kRMax][32] the pixel each owned class currently holds, or -1
+    int4* rec;               // [seg_len] entries, w replaced by the key
+    static constexpr size_t kFixed = 2 * kRMax * 32 * sizeof(int);
+    __device__ explicit WarpSmem(unsigned char* base)
+        : puv(reinterpret_cast<int (*)[32]>(base)),
+          cur(reinterpret_cast<int (*)[32]>(base) + kRMax),
+          rec(reinterpret_cast<int4*>(base + kFixed)) {}
+    static constexpr size_t bytes(int seg_len) { return kFixed + (size_t)seg_len * sizeof(int4); }
+};
 
-// A warp takes chunks of consecutive entries from a global counter, so that the overlapping
-// footprints of consecutive entries of a track are read by the same SM (L1 reuse).  Per entry
-// the lanes stride over the S x S footprint and accumulate conj(k) g as the packed pairs
-// A = (kx, kx) (gx, gy) and B = (ky, ky) (gx, gy): conj(k) g = (A.x + B.y, A.y - B.x).
-template <int P>
-__global__ void __launch_bounds__(256, 4) k_degrid(const int4* __restrict__ entries, const int2* __restrict__ runs,
-                                                const long long* __restrict__ scal, const int* __restrict__ supports,
-                                                const float2* __restrict__ table, const float2* __restrict__ grid,
-                                                int N, int C, int kst, const double* __restrict__ uvw,
-                                                const float* __restrict__ weight, const uint8_t* __restrict__ flag,
-                                                int adjoint, float2* __restrict__ out, int K, int64_t n_samples,
-                                                int64_t rows, int interleave, int cross_swap,
-                                                unsigned int* __restrict__ counter,
-                                                long long* __restrict__ dropped)
+// Sums v[0..V) over the warp and scatters the sums: lane l returns the total of component
+// l / (32 / V).  log2(V) halving exchanges (each lane sends the half it does not keep), then
+// xor-butterflies over the remaining lane bits.
+template <int V>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[V], int lane)
 {
-    const long long n = scal[0];
-    const int lane = threadIdx.x & 31;
-    for (;;) {
-        unsigned int chunk = 0;
-        if (lane == 0) chunk = atomicAdd(counter, 1u);
-        chunk = __shfl_sync(0xffffffffu, chunk, 0);
-        const long long c0 = (long long)chunk * kDegridChunk;
-        if (c0 >= n) break;
-        const long long c1 = min(n, c0 + kDegridChunk);
-        for (long long e = c0; e < c1; ++e) {
-            const int4 E = entries[e];
-            const int k = E.w & 0xFFF, gchan = (E.w >> 16) & 0xFFFF;
-            const int ch = gchan / kst;                  // input channel (w-stacking: kst planes each)
-            if (k >= K || ch >= C) {                 // device-side bounds checks (never taken)
-                if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
-                continue;
-            }
-            const int S = __ldg(&supports[k]);
-            const int x0 = E.x & 0xFFFF, y0 = (E.x >> 16) & 0xFFFF, z = E.z;
-            const int2 run = runs[e];
-            if (x0 + S > N || y0 + S > N || z < 0 || (int64_t)z + (int64_t)S * S > n_samples || run.x < 0 ||
-                run.y < run.x || (int64_t)run.y >= (interleave ? rows * C : rows)) {
-                if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
-                continue;
-            }
-            const float2* gch = grid + (size_t)gchan * N * N * P;   // channel 0 when interleaved
-            f32x2 A[P], B[P];
 #pragma unroll
-            for (int p = 0; p < P; ++p) A[p] = B[p] = 0ull;
-            const int s2 = S * S;
-            int i = lane / S, j = lane - (lane / S) * S;
-            const int di = 32 / S, dj = 32 - di * S;
-            for (int s = lane; s < s2; s += 32) {
-                const float2 kv = __ldg(&table[z + s]);
-                const f32x2 kxx = pack2(kv.x, kv.x), kyy = pack2(kv.y, kv.y);
-                f32x2 gv[P];
-                load_pixel<P>(gch + ((size_t)(y0 + i) * N + x0 + j) * P, gv);
+    for (int h = V / 2, m = 16; h >= 1; h >>= 1, m >>= 1) {
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = up ? v[i] : v[i + h];
+            const float keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
+    }
+    float s = v[0];
+#pragma unroll
+    for (int m = 16 / V; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    return s;
+}
+
+// Entries [j, e1) of the staged segment while their key (support, grid channel) equals `key`,
+// footprint block `blk`, R points per lane (RT > 0 fixes R at compile time; points past S^2
+// keep pixel value 0 and read sample offset 0).  Adds each entry's sums to acc[j][2P]; returns
+// the first entry not processed.
+template <int P, int RT>
+__device__ __forceinline__ int degrid_records(int j, int e1, int key, int S, int R, int blk, int N, int lane,
+                                              WarpSmem& sm, const float2* __restrict__ table,
+                                              const float2* __restrict__ gch, float* __restrict__ acc)
+{
+    constexpr int V = 2 * P;
+    if constexpr (RT > 0) R = RT;
+    f32x2 pv[kRMax][P];
+    int toff[kRMax];
+    unsigned valid = 0;
+    const int s2 = S * S, sbase = blk * 32 * R;
+#pragma unroll
+    for (int r = 0; r < kRMax; ++r) {
+        const int sl = sbase + r * 32 + lane;
+        sm.cur[r][lane] = -1;
+        toff[r] = 0;
+        if (r < R && sl < s2) {
+            valid |= 1u << r;
+            const int q = sl / S;
+            sm.puv[r][lane] = (sl - q * S) | (q << 16);
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) pv[r][p] = 0ull;
+    }
+    int fp = -1;             // footprint origin (x0 | y0 << 16) the offsets and pixels refer to
+    bool pre = false;        // the current buffer holds the current entry's samples (prefetched)
+    f32x2 kva[kRMax], kvb[kRMax];
+    auto step = [&](f32x2 (&cur_kv)[kRMax], f32x2 (&nxt)[kRMax]) -> bool {
+        if (j >= e1) return false;
+        const int4 E = sm.rec[j];
+        if (E.w != key) return false;
+        if (!pre) {
+            if (E.x != fp) {     // the footprint moved: new offsets, reload the pixels that change
+                const int x0 = E.x & 0xFFFF, y0 = (E.x >> 16) & 0xFFFF;
+                const int cu = E.y & 0xFFFF, cv = (E.y >> 16) & 0xFFFF;
+#pragma unroll
+                for (int r = 0; r < kRMax; ++r) {
+                    if (r < R && (valid & (1u << r))) {
+                        const int puv = sm.puv[r][lane];
+                        int du = (puv & 0xFFFF) + cu;
+                        du -= (du >= S) ? S : 0;
+                        int dv = (puv >> 16) + cv;
+                        dv -= (dv >= S) ? S : 0;
+                        toff[r] = dv * S + du;
+                        const int pix = (y0 + dv) * N + x0 + du;
+                        if (pix != sm.cur[r][lane]) {
+                            load_pixel<P>(gch + (size_t)pix * P, pv[r]);
+                            sm.cur[r][lane] = pix;
+                        }
+                    }
+                }
+                fp = E.x;
+            }
+            const f32x2* kz = reinterpret_cast<const f32x2*>(table + E.z);
+#pragma unroll
+            for (int r = 0; r < kRMax; ++r) {
+                if (RT == 0 && r >= R) break;
+                if (r < R) cur_kv[r] = __ldg(kz + toff[r]);
+            }
+        }
+        pre = false;
+        if (j + 1 < e1) {
+            const int4 E1 = sm.rec[j + 1];
+            if (E1.x == fp && E1.w == key) {
+                const f32x2* kz = reinterpret_cast<const f32x2*>(table + E1.z);
+#pragma unroll
+                for (int r = 0; r < kRMax; ++r) {
+                    if (RT == 0 && r >= R) break;
+                    if (r < R) nxt[r] = __ldg(kz + toff[r]);
+                }
+                pre = true;
+            }
+        }
+        // A_p = sum kx (gx, gy), B_p = sum ky (gx, gy); conj(k) g = (A.x + B.y, A.y - B.x)
+        f32x2 A[P], B[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) A[p] = B[p] = 0ull;
+#pragma unroll
+        for (int r = 0; r < kRMax; ++r) {
+            if (RT == 0 && r >= R) break;
+            if (r < R) {
+                const float2 k = unpack2(cur_kv[r]);
+                const f32x2 kxx = pack2(k.x, k.x), kyy = pack2(k.y, k.y);
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    A[p] = fma2(kxx, gv[p], A[p]);
-                    B[p] = fma2(kyy, gv[p], B[p]);
-                }
-                j += dj;
-                i += di;
-                if (j >= S) {
-                    j -= S;
-                    ++i;
-                }
-            }
-            float2 acc[P];
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const float2 a = unpack2(A[p]), b = unpack2(B[p]);
-                acc[p] = make_float2(a.x + b.y, a.y - b.x);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    acc[p].x += __shfl_xor_sync(0xffffffffu, acc[p].x, o);
-                    acc[p].y += __shfl_xor_sync(0xffffffffu, acc[p].y, o);
-                }
-            }
-            // the run's records: rows run.x..run.y of channel ch, or records run.x..run.y
-            for (int r = run.x + lane; r <= run.y; r += 32) {
-                const int64_t rec = interleave ? (int64_t)r : (int64_t)r * C + ch;
-                const int64_t row = interleave ? (int64_t)r / C : (int64_t)r;
-                const bool neg = uvw[3 * row + 2] < 0.0;
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    // with cross-hand swapping, output pol 1 of a take-conjugate record comes from
-                    // grid pol 2 and pol 2 from pol 1 (the adjoint of the swap is the swap)
-                    float2 a = acc[p];
-                    if constexpr (P == 4) {
-                        if (cross_swap && neg && p == 1) a = acc[2];
-                        if (cross_swap && neg && p == 2) a = acc[1];
-                    }
-                    float2 v = neg ? make_float2(a.x, -a.y) : a;
-                    if (adjoint) {
-                        const float wf = weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
-                        v.x *= wf;
-                        v.y *= wf;
-                    }
-                    out[rec * P + p] = v;
+                    A[p] = fma2(kxx, pv[r][p], A[p]);
+                    B[p] = fma2(kyy, pv[r][p], B[p]);
                 }
             }
         }
+        float v[V];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float2 a = unpack2(A[p]), b = unpack2(B[p]);
+            v[2 * p] = a.x + b.y;
+            v[2 * p + 1] = a.y - b.x;
+        }
+        const float s = warp_reduce_scatter<V>(v, lane);
+        if ((lane & (32 / V - 1)) == 0) atomicAdd(acc + (size_t)j * V + lane / (32 / V), s);
+        ++j;
+        return true;
+    };
+    for (;;) {
+        if (!step(kva, kvb)) break;
+        if (!step(kvb, kva)) break;
     }
+    return j;
+}
+
+// An entry's placement is consistent with the table and the grid (the checks of the gridder's
+// staging; never false for a work list written by vis_compress for this table and grid).
+__device__ __forceinline__ bool entry_ok(const int4& E, const int* __restrict__ supports, int N, int K, int C,
+                                         int64_t n_samples)
+{
+    const int k = E.w & 0xFFF, ch = (E.w >> 16) & 0xFFFF;
+    if (E.w < 0 || k >= K || ch >= C) return false;
+    const int S = __ldg(&supports[k]);
+    const int x0 = E.x & 0xFFFF, y0 = (E.x >> 16) & 0xFFFF;
+    const int cu = E.y & 0xFFFF, cv = (E.y >> 16) & 0xFFFF;
+    return x0 + S <= N && y0 + S <= N && cu < S && cv < S && E.z >= 0 &&
+           (int64_t)E.z + (int64_t)S * S <= n_samples;
+}
+
+}  // namespace
+
+// acc[0 .. n_entries * 2P) = 0
+__global__ void k_degrid_zero(float4* __restrict__ acc, const long long* __restrict__ scal, int P)
+{
+    const long long n4 = scal[0] * P / 2;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x)
+        acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+template <int P, int RT>
+__global__ void __launch_bounds__(kWarps * 32, P == 4 ? 3 : 4) k_degrid_sum(const int4* __restrict__ entries,
+                                                               const int* __restrict__ seg_off,
+                                                               const long long* __restrict__ scal,
+                                                               const int* __restrict__ supports,
+                                                               const float2* __restrict__ table,
+                                                               const float2* __restrict__ grid, int N, int K, int C,
+                                                               int64_t n_samples, int seg_len, int slots,
+                                                               unsigned int* __restrict__ counter,
+                                                               float* __restrict__ acc)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    WarpSmem sm(smem_raw + (size_t)wid * WarpSmem::bytes(seg_len));
+    const long long n_entries = scal[0], n_tasks = scal[1], n_seg = scal[2];
+    const size_t chan_stride = (size_t)N * N * P;
+
+    for (;;) {
+        unsigned int t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if ((long long)t >= n_tasks) break;
+        int lo = 0, hi = (int)n_seg;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(&seg_off[mid]) <= (int)t) lo = mid; else hi = mid;
+        }
+        const int blk = (int)t - __ldg(&seg_off[lo]);
+        const int e0 = lo * seg_len;
+        const int n = (int)min((long long)seg_len, n_entries - e0);
+
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) cp_async16(&sm.rec[i], entries + e0 + i);
+        asm volatile("cp.async.commit_group;\n" ::);
+        asm volatile("cp.async.wait_group 0;\n" ::);
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const int4 E = sm.rec[i];
+            sm.rec[i].w = entry_ok(E, supports, N, K, C, n_samples)
+                              ? (__ldg(&supports[E.w & 0xFFF]) << 16) | ((E.w >> 16) & 0xFFFF)
+                              : -1;
+        }
+        __syncwarp();
+
+        int j = 0;
+        while (j < n) {
+            const int key = sm.rec[j].w;
+            if (key < 0) {
+                ++j;
+                continue;
+            }
+            const int S = key >> 16, ch = key & 0xFFFF;
+            const int s2 = S * S;
+            const int nb = (s2 + slots - 1) / slots;
+            const int R = RT > 0 ? RT : (s2 + 32 * nb - 1) / (32 * nb);
+            if (blk >= nb) {     // this block has no points for this support: skip the run
+                while (j < n && sm.rec[j].w == key) ++j;
+                continue;
+            }
+            j = degrid_records<P, RT>(j, n, key, S, R, blk, N, lane, sm, table, grid + (size_t)ch * chan_stride,
+                                      acc + (size_t)e0 * 2 * P);
+        }
+    }
+}
+
+// One thread per entry writes the records of its run: rows run.x..run.y of input channel
+// gchan / kst (w-stacking: kst planes per channel), or records run.x..run.y when interleaved.
+template <int P>
+__global__ void k_degrid_out(const int4* __restrict__ entries, const int2* __restrict__ runs,
+                             const long long* __restrict__ scal, const int* __restrict__ supports,
+                             const float2* __restrict__ acc, int N, int K, int Cg, int C, int kst, int64_t n_samples,
+                             const double* __restrict__ uvw, const float* __restrict__ weight,
+                             const uint8_t* __restrict__ flag, int adjoint, float2* __restrict__ out, int64_t rows,
+                             int interleave, int cross_swap, long long* __restrict__ dropped)
+{
+    const long long n = scal[0];
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int4 E = entries[e];
+        const int2 run = runs[e];
+        const int ch = ((E.w >> 16) & 0xFFFF) / kst;
+        if (!entry_ok(E, supports, N, K, Cg, n_samples) || ch >= C || run.x < 0 || run.y < run.x ||
+            (int64_t)run.y >= (interleave ? rows * C : rows)) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
+            continue;
+        }
+        float2 m[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) m[p] = acc[e * P + p];
+        for (int r = run.x; r <= run.y; ++r) {
+            const int64_t rec = interleave ? (int64_t)r : (int64_t)r * C + ch;
+            const int64_t row = interleave ? (int64_t)r / C : (int64_t)r;
+            const bool neg = uvw[3 * row + 2] < 0.0;
+            float2 v[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                // with cross-hand swapping, output pol 1 of a take-conjugate record comes from
+                // grid pol 2 and pol 2 from pol 1 (the adjoint of the swap is the swap)
+                float2 a = m[p];
+                if constexpr (P == 4) {
+                    if (cross_swap && neg && p == 1) a = m[2];
+                    if (cross_swap && neg && p == 2) a = m[1];
+                }
+                v[p] = neg ? make_float2(a.x, -a.y) : a;
+                if (adjoint) {
+                    const float wf = weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
+                    v[p].x *= wf;
+                    v[p].y *= wf;
+                }
+            }
+            float2* o = out + rec * P;
+            if constexpr (P == 1) {
+                o[0] = v[0];
+            } else {
+#pragma unroll
+                for (int h = 0; h < P; h += 2)
+                    *reinterpret_cast<float4*>(o + h) = make_float4(v[h].x, v[h].y, v[h + 1].x, v[h + 1].y);
+            }
+        }
+    }
+}
+
+template <int P, int RT>
+static int degrid_sum_launch(const Grid& g, const Table& t, const WorkList& wl, cudaStream_t s)
+{
+    static int blocks_per_sm[kSegLenMax / kSegLenMin + 1] = {0};
+    const int smem = (int)(kWarps * WarpSmem::bytes(wl.seg_len));
+    int& bps = blocks_per_sm[wl.seg_len / kSegLenMin];
+    if (bps == 0) {
+        WG_CUDA(cudaFuncSetAttribute(k_degrid_sum<P, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kWarps * WarpSmem::bytes(kSegLenMax))));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_degrid_sum<P, RT>, kWarps * 32, smem) !=
+                cudaSuccess ||
+            bps < 1)
+            bps = 1;
+    }
+    k_degrid_sum<P, RT><<<num_sms() * bps, kWarps * 32, smem, s>>>(
+        wl.entries, wl.seg_off, wl.scal, t.supports_d, t.data, g.data, g.n, t.K, g.n_chan, t.n_samples, wl.seg_len,
+        wl.slots, wl.task_counter + 1, reinterpret_cast<float*>(wl.dacc));
+    WG_LAUNCHED("k_degrid_sum");
+    return WG_OK;
 }
 
 template <int P>
 static int degrid_impl(const Grid& g, const Table& t, const wg_vis_in& in, const WorkList& wl, int mode, float2* out,
                        cudaStream_t s)
 {
+    if (!wl.dacc) return fail(WG_E_INVALID_ARG, "degrid_vis: the work list has no degridding accumulator");
     WG_CUDA(cudaMemsetAsync(out, 0, sizeof(float2) * (size_t)in.n_rows * in.n_chan * P, s));
     WG_CUDA(cudaMemsetAsync(wl.task_counter + 1, 0, sizeof(unsigned int), s));
-    static int blocks_per_sm = 0;
-    if (blocks_per_sm == 0 &&
-        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_degrid<P>, 256, 0) != cudaSuccess ||
-         blocks_per_sm < 1))
-        blocks_per_sm = 1;
-    const int blocks = num_sms() * blocks_per_sm;
-    k_degrid<P><<<blocks, 256, 0, s>>>(wl.entries, wl.runs, wl.scal, t.supports_d, t.data, g.data, g.n, in.n_chan,
-                                       wl.wstack_k,
-                                       in.uvw, in.weight, in.flag, mode == WG_DEGRID_ADJOINT ? 1 : 0, out, t.K,
-                                       t.n_samples, in.n_rows, wl.interleave ? 1 : 0, wl.cross_swap ? 1 : 0,
-                                       wl.task_counter + 1,
-                                       wl.scal + 3);
-    WG_LAUNCHED("k_degrid");
+    const int zb = num_sms() * 4;
+    k_degrid_zero<<<zb, 256, 0, s>>>(reinterpret_cast<float4*>(wl.dacc), wl.scal, P);
+    WG_LAUNCHED("k_degrid_zero");
+    int rc;
+    if (wl.fixed_r && wl.slots == 256) rc = degrid_sum_launch<P, 8>(g, t, wl, s);
+    else if (wl.fixed_r && wl.slots == 128) rc = degrid_sum_launch<P, 4>(g, t, wl, s);
+    else rc = degrid_sum_launch<P, 0>(g, t, wl, s);
+    if (rc != WG_OK) return rc;
+    k_degrid_out<P><<<num_sms() * 8, 256, 0, s>>>(wl.entries, wl.runs, wl.scal, t.supports_d, wl.dacc, g.n, t.K,
+                                                  g.n_chan, in.n_chan, wl.wstack_k, t.n_samples, in.uvw, in.weight,
+                                                  in.flag, mode == WG_DEGRID_ADJOINT ? 1 : 0, out, in.n_rows,
+                                                  wl.interleave ? 1 : 0, wl.cross_swap ? 1 : 0, wl.scal + 3);
+    WG_LAUNCHED("k_degrid_out");
     return WG_OK;
 }
 

@@ -114,6 +114,7 @@ struct WorkList {
     int4* entries = nullptr;
     float2* gamma = nullptr;
     int2* runs = nullptr;
+    float2* dacc = nullptr;               // [cap][P] degridding sums per entry (not in no-alloc views)
     // segments
     int* seg_nblk = nullptr;
     int* seg_off = nullptr;               // [seg_cap + 1]
