@@ -185,6 +185,27 @@ def whole_job_rate(units_per_rank, ms, world):
     return world * units_per_rank / (ms * 1e-3) / 1e9
 
 
+def measured_ceilings(real_rate: float, P: int) -> dict:
+    """The two ceilings of the gridder's roofline, measured on this device by the library's
+    microbenchmarks (ceiling_measure): the FP32 FMA rate (8 flops per update) and the kernel-
+    sample fetch bandwidth (one 8-byte sample per point and record, shared by P polarisations),
+    with the gridder's real update rate against each and against the lower of the two."""
+    import paper_1403_4209_gb300 as wg
+    c = {k: wg.ceiling(k) for k in ("fp32_fma2", "fp32_fma", "fetch_l1", "fetch_l2", "shared")}
+    fma = max(c["fp32_fma2"], c["fp32_fma"]) / 8.0
+    l1, l2 = c["fetch_l1"] * P / 8.0, c["fetch_l2"] * P / 8.0
+    low = min(fma, l2)
+    return {"fp32_fma2_tflops": round(c["fp32_fma2"] / 1e12, 2), "fp32_fma_tflops": round(c["fp32_fma"] / 1e12, 2),
+            "fetch_l1_tbs": round(c["fetch_l1"] / 1e12, 2), "fetch_l2_tbs": round(c["fetch_l2"] / 1e12, 2),
+            "shared_tbs": round(c["shared"] / 1e12, 2),
+            "updates_ceiling_fma_G": round(fma / 1e9, 1), "updates_ceiling_fetch_l2_G": round(l2 / 1e9, 1),
+            "updates_ceiling_fetch_l1_G": round(l1 / 1e9, 1), "bound": "fma" if fma <= l2 else "fetch_l2",
+            "frac_of_fma": round(real_rate / fma, 4), "frac_of_fetch_l2": round(real_rate / l2, 4),
+            "frac_of_min": round(real_rate / low, 4),
+            "note": "real gridder updates/s against measured ceilings; kernel samples stream mostly from L2 "
+                    "(ncu l1tex hit rate about 16 %), so the fetch ceiling is the L2 one"}
+
+
 def _gridder_traffic(per_launch_units):
     """DRAM bytes per k_grid launch from the committed ncu summary, scaled to this launch's
     gridded updates; None if the gridder source changed since the counters were taken."""
@@ -467,6 +488,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak_source": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flops x %.0f MHz (%s sm_max_mhz)"
                                     % (props.multi_processor_count, sm_mhz, src),
                      "traffic": traffic},
+        "ceilings": measured_ceilings(real / (t_grid * 1e-3), wl.n_pol),
         "variants": variants,
         "e2e": {"value": round(whole_job_rate(total, ms_e2e, world), 3), "unit": "G grid-point updates/s",
                 "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -591,6 +613,7 @@ def run_batch(args, rank, world, local_rank):
                      "peak_source": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flops x %.0f MHz (%s sm_max_mhz)"
                                     % (props.multi_processor_count, sm_mhz, src),
                      "traffic": None},
+        "ceilings": measured_ceilings(real / (t_grid * 1e-3), wl.n_pol),
         "e2e": None,
         "gpu_launches": int(captured * args.steps),
         "graph": {"captured_launches_per_step": int(captured), "replays": args.steps},
@@ -916,6 +939,77 @@ def run_reference(args):
     }
 
 
+# The thesis's experiment batches 2-4 (Sec. 5.4, tables "batch2" / "batch3" / "batch4"):
+# the real gridding rate per convolution-function size as the uv cell (grid side N at a fixed
+# uv extent), the oversampling factor and the number of polarisations vary.  One plane (K = 1)
+# with a prescribed support S isolates the support; the geometry is the 2-channel slice of the
+# w-projection workload (2016 baselines x 3600 steps, 120 and 124 MHz).
+SWEEPS = {
+    "support": [dict(N=2048, beta=8, pols=4, S=S) for S in (7, 15, 31, 63, 127)],
+    "oversample": [dict(N=2048, beta=b, pols=4, S=S) for S in (15, 63) for b in (2, 4, 8)],
+    "grid": [dict(N=n, beta=8, pols=4, S=S) for S in (15, 63) for n in (1024, 2048, 4096)],
+    "pols": [dict(N=2048, beta=8, pols=p, S=S) for S in (15, 63) for p in (1, 2, 4)],
+}
+SWEEP_POLS = {1: [0], 2: [0, 3], 4: [0, 1, 2, 3]}
+
+
+def run_sweep(args):
+    """One JSON line per sweep point: records, compression, plan, real and total gridder rates
+    (CUDA events over 5 launches after grid_autotune), preparation time."""
+    import dataclasses
+
+    import torch
+
+    import paper_1403_4209_gb300 as wg
+    import synth
+    dev = "cuda"
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    base = synth.make("wproj_2k", device=dev, n_chan=2, n_times=args.n_times)
+    du0 = base.du                     # cell at N = 2048: the uv extent stays fixed as N varies
+    uvw_d, freq_d = torch.as_tensor(base.uvw, device=dev), torch.as_tensor(base.freq, device=dev)
+    names = list(SWEEPS) if args.sweep == "all" else [args.sweep]
+    for name in names:
+        for pt in SWEEPS[name]:
+            N, beta, S, pols = pt["N"], pt["beta"], pt["S"], SWEEP_POLS[pt["pols"]]
+            du = du0 * 2048 / N
+            wl = dataclasses.replace(base, vis=base.vis[..., pols].contiguous(),
+                                     weight=base.weight[..., pols].contiguous(),
+                                     flag=base.flag[..., pols].contiguous())
+            P = len(pols)
+            tab = wg.ConvTable.build(du, 1, wl.w_max, beta, wl.taper_support, supports=[S])
+            g = wg.Grid(N, du, P, wl.n_chan, device=dev)
+            batch = wg.VisBatch(uvw_d, freq_d, wl.vis, wl.weight, wl.flag)
+            wlst = wg.WorkList(wl.rows * wl.n_chan, wl.n_chan, P)
+            wg.vis_compress(g, tab, batch, wlst)
+            plan = wg.grid_autotune(g, tab, wlst, repeats=2)
+            st = wlst.stats()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            for _ in range(2):
+                wg.vis_compress(g, tab, batch, wlst)
+            ev[0].record(stream)
+            for _ in range(5):
+                wg.vis_compress(g, tab, batch, wlst)
+            ev[1].record(stream)
+            ev[2].record(stream)
+            for _ in range(5):
+                wg.grid_vis(g, tab, wlst)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            t_prep, t_grid = ev[0].elapsed_time(ev[1]) / 5, ev[2].elapsed_time(ev[3]) / 5
+            real, total = st["updates"], st["updates"] + st["updates_saved"]
+            print(json.dumps({
+                "sweep": name, "N": N, "beta": beta, "n_pol": P, "support": S, "du": round(du, 4),
+                "records": st["records"], "griddable": st["griddable"], "gridded": st["gridded"],
+                "compression_ratio_records": round(st["compressed"] / max(1, st["gridded"]), 3),
+                "plan_seg_len_slots_fixed_r": list(plan[:3]), "prep_ms": round(t_prep, 3),
+                "gridder_ms": round(t_grid, 3), "real_gridder_G": round(real / (t_grid * 1e-3) / 1e9, 1),
+                "total_gridder_G": round(total / (t_grid * 1e-3) / 1e9, 1),
+                "record_rate_real_M": round(st["gridded"] / (t_grid * 1e-3) / 1e6, 1)}), flush=True)
+            del tab, g, wlst, wl, batch
+            torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -928,6 +1022,9 @@ def main():
     ap.add_argument("--n-chan", type=int, default=None, help="run a slice: first n channels (profiling)")
     ap.add_argument("--n-times", type=int, default=None, help="run a slice: n time steps (profiling)")
     ap.add_argument("--chan0", type=int, default=0, help="first channel of an --n-chan slice")
+    ap.add_argument("--sweep", choices=sorted(SWEEPS) + ["all"], default=None,
+                    help="instead of the benchmark line, the rate sweeps of the thesis's experiment batches 2-4 "
+                         "(one JSON line per point)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -937,6 +1034,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+    if args.sweep:
+        if rank == 0:
+            run_sweep(args)
         return
     if world > 1:
         import torch

@@ -400,6 +400,27 @@ typedef struct wg_grid_view {
 int grid_vis_noalloc(const wg_grid_view* grid, const wg_table* table, const wg_vis_in* in,
                      int32_t compress, void* stream);
 
+/* ---- roofline ceilings (measurement; not in the thesis) ------------------------------
+ * Gridding does 8 flops per update (one complex multiply-add, Sec. 5.4.4) and fetches one
+ * 8-byte kernel sample per footprint point and record, shared by the n_pol polarisations, so
+ * its ceilings are the FP32 FMA rate and the bandwidth of 8-byte read-only loads.  Each kind
+ * times one launch of a microbenchmark kernel over every SM (8 blocks of 256 threads per SM),
+ * after a warm-up launch, with CUDA events on the legacy default stream of the current device:
+ *   FP32_FMA2: FLOP/s of independent packed FMAs (fma.rn.f32x2, 4 flops each);
+ *   FP32_FMA:  FLOP/s of independent scalar FMAs (2 flops each);
+ *   FETCH_L1:  bytes/s of warp-wide 8-byte __ldg loads of 256 contiguous bytes at warp-uniform
+ *              pseudo-random positions in a 64 KB buffer (L1-resident);
+ *   FETCH_L2:  the same in a 32 MB buffer (L2-resident, L1 hit rate about 0);
+ *   SHARED:    bytes/s of warp-wide 8-byte shared-memory loads of 256 contiguous bytes.
+ * Synchronous: allocates and frees its scratch (at most 32 MB), returns after the timing.
+ * value: host double.  Errors: INVALID_ARG, OOM, CUDA. */
+#define WG_CEIL_FP32_FMA2 1
+#define WG_CEIL_FP32_FMA 2
+#define WG_CEIL_FETCH_L1 3
+#define WG_CEIL_FETCH_L2 4
+#define WG_CEIL_SHARED 5
+int ceiling_measure(int32_t kind, double* value);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,12 +11,12 @@ marshals torch tensors into its C ABI.
 from ._lib import CONST, WgError, header_functions, lib
 from .api import (DEGRID_ADJOINT, DEGRID_PREDICT, IMAGE_PER_POL, IMAGE_PER_POL_RAW, IMAGE_STOKES_CIRCULAR, IMAGE_STOKES_I,
                   IMAGE_STOKES_LINEAR, IMAGE_TRANSPOSE, IMAGE_WSTACK,
-                  ConvTable, Grid, VisBatch, WorkList, degrid_vis, grid_autotune, grid_correct, grid_vis, vis_weight, image_to_grid, launch_count,
+                  ConvTable, Grid, VisBatch, WorkList, ceiling, degrid_vis, grid_autotune, grid_correct, grid_vis, vis_weight, image_to_grid, launch_count,
                   vis_compress)
 from .autograd import DegridFn, SkyModel
 
 __all__ = [
     "CONST", "WgError", "header_functions", "lib", "DEGRID_ADJOINT", "DEGRID_PREDICT", "IMAGE_PER_POL",
     "IMAGE_STOKES_I", "IMAGE_PER_POL_RAW", "IMAGE_TRANSPOSE", "IMAGE_STOKES_LINEAR", "IMAGE_STOKES_CIRCULAR", "IMAGE_WSTACK", "ConvTable", "Grid", "VisBatch", "WorkList",
-    "degrid_vis", "grid_autotune", "grid_correct", "vis_weight", "grid_vis", "image_to_grid", "launch_count", "vis_compress", "DegridFn", "SkyModel",
+    "ceiling", "degrid_vis", "grid_autotune", "grid_correct", "vis_weight", "grid_vis", "image_to_grid", "launch_count", "vis_compress", "DegridFn", "SkyModel",
 ]

@@ -66,7 +66,7 @@ def header_functions():
 
 def _load():
     path = _build.LIB
-    if not os.path.exists(path):
+    if _build.stale():
         try:
             _build.build()
         except Exception as e:  # noqa: BLE001
@@ -99,6 +99,7 @@ def _load():
         "degrid_vis": (c_i32, [c_vp, c_vp, P(VisIn), c_vp, c_i32, c_vp, c_vp]),
         "grid_correct": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
         "vis_weight": (c_i32, [c_vp, c_vp, P(VisIn), c_i32, c_dbl, c_i32, c_vp, c_vp]),
+        "ceiling_measure": (c_i32, [c_i32, P(c_dbl)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(so, name)

@@ -57,6 +57,18 @@ def launch_count() -> int:
     return int(lib.wg_launch_count())
 
 
+CEILINGS = {"fp32_fma2": "WG_CEIL_FP32_FMA2", "fp32_fma": "WG_CEIL_FP32_FMA", "fetch_l1": "WG_CEIL_FETCH_L1",
+            "fetch_l2": "WG_CEIL_FETCH_L2", "shared": "WG_CEIL_SHARED"}
+
+
+def ceiling(kind: str) -> float:
+    """Measured roofline ceiling on the current device (ceiling_measure): FLOP/s for
+    "fp32_fma2" / "fp32_fma", bytes/s for "fetch_l1" / "fetch_l2" / "shared".  Synchronous."""
+    v = ctypes.c_double()
+    check(lib.ceiling_measure(CONST[CEILINGS[kind]], ctypes.byref(v)), "ceiling_measure")
+    return float(v.value)
+
+
 class Grid:
     """Complex64 uv-grids [n_chan][N][N][n_pol] (torch tensor `data`) plus FP64 normalisers."""
 

@@ -35,9 +35,19 @@ def _stale(srcs, deps):
     return any(os.path.getmtime(p) > t for p in srcs + deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+def _inputs():
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     deps = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "wgrid.h"), __file__]
+    return srcs, deps
+
+
+def stale() -> bool:
+    """True when libwgrid.so is missing or older than a source, header or this script."""
+    return _stale(*_inputs())
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+    srcs, deps = _inputs()
     if not force and not _stale(srcs, deps):
         return LIB
     os.makedirs(BUILD, exist_ok=True)

@@ -84,3 +84,11 @@ def test_plan_limits_and_null_handles():
     assert "null" in _err()
     assert wg.lib.worklist_get_plan(None, None) == C["WG_E_INVALID_ARG"]
     assert wg.lib.grid_autotune(None, None, None, None, 0, 3, None, None, None) == C["WG_E_INVALID_ARG"]
+
+
+def test_ceiling_rejects_bad_arguments():
+    v = ctypes.c_double(1.0)
+    assert wg.lib.ceiling_measure(0, ctypes.byref(v)) == C["WG_E_INVALID_ARG"] and "unknown ceiling" in _err()
+    assert wg.lib.ceiling_measure(C["WG_CEIL_SHARED"] + 1, ctypes.byref(v)) == C["WG_E_INVALID_ARG"]
+    assert v.value == 0.0
+    assert wg.lib.ceiling_measure(C["WG_CEIL_FP32_FMA2"], None) == C["WG_E_INVALID_ARG"]

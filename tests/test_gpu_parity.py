@@ -7,6 +7,8 @@ Bars (written here, derived in the design doc):
     N_p within 1e-5 relative.
 Sizes span several prep tiles, gridder segments and warps, with ragged tails.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -183,3 +185,18 @@ def test_cell_boundaries_bit_exact(du):
     # the entries carry the sub-cell through z: compare it with the oracle's directly
     g = np.nonzero(pl.griddable)[0]
     assert np.array_equal(np.sort(gp["entries"][:, 2]), np.sort(pl.z[g]))
+
+
+@pytest.mark.parametrize("N,beta,pols,S", [(2048, 2, 4, 15), (2048, 4, 4, 63), (1024, 8, 2, 31), (4096, 8, 1, 127),
+                                           (1024, 2, 1, 7)])
+def test_sweep_configurations(N, beta, pols, S):
+    # the configurations of bench.py's rate sweeps (the thesis's experiment batches 2-4): one
+    # plane with a prescribed support, oversampling 2-8, 1-4 polarisations, grid side 1024-4096
+    # at the uv extent of the 2048 grid (at 1024 the outer tracks leave the grid)
+    base = synth.make("wproj_2k", n_times=40, n_chan=2, n_baselines=300, flag_frac=0.01)
+    sel = {1: [0], 2: [0, 3], 4: [0, 1, 2, 3]}[pols]
+    wl = dataclasses.replace(base, vis=base.vis[..., sel].contiguous(), weight=base.weight[..., sel].contiguous(),
+                             flag=base.flag[..., sel].contiguous(), n_grid=N, du=base.du * 2048 / N,
+                             oversample=beta, n_wplanes=1, supports=[S])
+    gp, o = _check(wl, True)
+    assert gp["stats"]["compressed"] > 0
