@@ -75,12 +75,10 @@ __device__ __forceinline__ void load_pixel(const float2* __restrict__ g, f32x2 (
 // Per-warp shared memory: the residue-class arrays, then the segment's staged entries.
 struct WarpSmem {
     int (*puv)[32];          // [kRMax][32] each lane's owned residue classes (pu | pv << 16)
-    int (*cur)[32];          // [kRMax][32] the pixel each owned class currently holds, or -1
     int4* rec;               // [seg_len] entries, w replaced by the key
-    static constexpr size_t kFixed = 2 * kRMax * 32 * sizeof(int);
+    static constexpr size_t kFixed = kRMax * 32 * sizeof(int);
     __device__ explicit WarpSmem(unsigned char* base)
         : puv(reinterpret_cast<int (*)[32]>(base)),
-          cur(reinterpret_cast<int (*)[32]>(base) + kRMax),
           rec(reinterpret_cast<int4*>(base + kFixed)) {}
     static constexpr size_t bytes(int seg_len) { return kFixed + (size_t)seg_len * sizeof(int4); }
 };
@@ -119,13 +117,13 @@ __device__ __forceinline__ int degrid_records(int j, int e1, int key, int S, int
     constexpr int V = 2 * P;
     if constexpr (RT > 0) R = RT;
     f32x2 pv[kRMax][P];
-    int toff[kRMax];
+    int toff[kRMax], cur[kRMax];     // sample offset and pixel held of each owned class
     unsigned valid = 0;
     const int s2 = S * S, sbase = blk * 32 * R;
 #pragma unroll
     for (int r = 0; r < kRMax; ++r) {
         const int sl = sbase + r * 32 + lane;
-        sm.cur[r][lane] = -1;
+        cur[r] = -1;
         toff[r] = 0;
         if (r < R && sl < s2) {
             valid |= 1u << r;
@@ -136,53 +134,36 @@ __device__ __forceinline__ int degrid_records(int j, int e1, int key, int S, int
         for (int p = 0; p < P; ++p) pv[r][p] = 0ull;
     }
     int fp = -1;             // footprint origin (x0 | y0 << 16) the offsets and pixels refer to
-    bool pre = false;        // the current buffer holds the current entry's samples (prefetched)
-    f32x2 kva[kRMax], kvb[kRMax];
-    auto step = [&](f32x2 (&cur_kv)[kRMax], f32x2 (&nxt)[kRMax]) -> bool {
-        if (j >= e1) return false;
+    for (; j < e1; ++j) {
         const int4 E = sm.rec[j];
-        if (E.w != key) return false;
-        if (!pre) {
-            if (E.x != fp) {     // the footprint moved: new offsets, reload the pixels that change
-                const int x0 = E.x & 0xFFFF, y0 = (E.x >> 16) & 0xFFFF;
-                const int cu = E.y & 0xFFFF, cv = (E.y >> 16) & 0xFFFF;
-#pragma unroll
-                for (int r = 0; r < kRMax; ++r) {
-                    if (r < R && (valid & (1u << r))) {
-                        const int puv = sm.puv[r][lane];
-                        int du = (puv & 0xFFFF) + cu;
-                        du -= (du >= S) ? S : 0;
-                        int dv = (puv >> 16) + cv;
-                        dv -= (dv >= S) ? S : 0;
-                        toff[r] = dv * S + du;
-                        const int pix = (y0 + dv) * N + x0 + du;
-                        if (pix != sm.cur[r][lane]) {
-                            load_pixel<P>(gch + (size_t)pix * P, pv[r]);
-                            sm.cur[r][lane] = pix;
-                        }
-                    }
-                }
-                fp = E.x;
-            }
-            const f32x2* kz = reinterpret_cast<const f32x2*>(table + E.z);
+        if (E.w != key) break;
+        if (E.x != fp) {     // the footprint moved: new offsets, reload the pixels that change
+            const int x0 = E.x & 0xFFFF, y0 = (E.x >> 16) & 0xFFFF;
+            const int cu = E.y & 0xFFFF, cv = (E.y >> 16) & 0xFFFF;
 #pragma unroll
             for (int r = 0; r < kRMax; ++r) {
-                if (RT == 0 && r >= R) break;
-                if (r < R) cur_kv[r] = __ldg(kz + toff[r]);
-            }
-        }
-        pre = false;
-        if (j + 1 < e1) {
-            const int4 E1 = sm.rec[j + 1];
-            if (E1.x == fp && E1.w == key) {
-                const f32x2* kz = reinterpret_cast<const f32x2*>(table + E1.z);
-#pragma unroll
-                for (int r = 0; r < kRMax; ++r) {
-                    if (RT == 0 && r >= R) break;
-                    if (r < R) nxt[r] = __ldg(kz + toff[r]);
+                if (r < R && (valid & (1u << r))) {
+                    const int puv = sm.puv[r][lane];
+                    int du = (puv & 0xFFFF) + cu;
+                    du -= (du >= S) ? S : 0;
+                    int dv = (puv >> 16) + cv;
+                    dv -= (dv >= S) ? S : 0;
+                    toff[r] = dv * S + du;
+                    const int pix = (y0 + dv) * N + x0 + du;
+                    if (pix != cur[r]) {
+                        load_pixel<P>(gch + (size_t)pix * P, pv[r]);
+                        cur[r] = pix;
+                    }
                 }
-                pre = true;
             }
+            fp = E.x;
+        }
+        f32x2 kv[kRMax];
+        const f32x2* kz = reinterpret_cast<const f32x2*>(table + E.z);
+#pragma unroll
+        for (int r = 0; r < kRMax; ++r) {
+            if (RT == 0 && r >= R) break;
+            if (r < R) kv[r] = __ldg(kz + toff[r]);
         }
         // A_p = sum kx (gx, gy), B_p = sum ky (gx, gy); conj(k) g = (A.x + B.y, A.y - B.x)
         f32x2 A[P], B[P];
@@ -192,7 +173,7 @@ __device__ __forceinline__ int degrid_records(int j, int e1, int key, int S, int
         for (int r = 0; r < kRMax; ++r) {
             if (RT == 0 && r >= R) break;
             if (r < R) {
-                const float2 k = unpack2(cur_kv[r]);
+                const float2 k = unpack2(kv[r]);
                 const f32x2 kxx = pack2(k.x, k.x), kyy = pack2(k.y, k.y);
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
@@ -208,14 +189,8 @@ __device__ __forceinline__ int degrid_records(int j, int e1, int key, int S, int
             v[2 * p] = a.x + b.y;
             v[2 * p + 1] = a.y - b.x;
         }
-        const float s = warp_reduce_scatter<V>(v, lane);
-        if ((lane & (32 / V - 1)) == 0) atomicAdd(acc + (size_t)j * V + lane / (32 / V), s);
-        ++j;
-        return true;
-    };
-    for (;;) {
-        if (!step(kva, kvb)) break;
-        if (!step(kvb, kva)) break;
+        const float sum = warp_reduce_scatter<V>(v, lane);
+        if ((lane & (32 / V - 1)) == 0) atomicAdd(acc + (size_t)j * V + lane / (32 / V), sum);
     }
     return j;
 }
@@ -245,7 +220,7 @@ __global__ void k_degrid_zero(float4* __restrict__ acc, const long long* __restr
 }
 
 template <int P, int RT>
-__global__ void __launch_bounds__(kWarps * 32, P == 4 ? 3 : 4) k_degrid_sum(const int4* __restrict__ entries,
+__global__ void __launch_bounds__(kWarps * 32, 4) k_degrid_sum(const int4* __restrict__ entries,
                                                                const int* __restrict__ seg_off,
                                                                const long long* __restrict__ scal,
                                                                const int* __restrict__ supports,

@@ -12,8 +12,7 @@
 // Fast path: consecutive gridded entries of a track usually keep the same footprint origin and
 // differ only in the sub-kernel z (about 85% of them, weighted by S^2, in the benchmark
 // workload).  Then each point's kernel offset toff = dv S + du and pixel are unchanged: the lane
-// only loads C[z + toff] and does 4P FMAs, and the next record's samples are prefetched into
-// registers while the current record's FMAs run.  When the footprint moves, the lane recomputes
+// only loads C[z + toff] and does 4P FMAs.  When the footprint moves, the lane recomputes
 // its offsets with the modular wrap and flushes the pixels that changed.  The segment's entries
 // and weighted visibilities are staged in shared memory once per task (cp.async).  R (points per
 // lane) is chosen per run of records with the same support and channel, or fixed per launch.
@@ -41,7 +40,7 @@ struct StagedRec {
 template <int P>
 struct WarpSmem {
     int (*puv)[32];          // [kRMax][32] each lane's owned residue classes (pu | pv << 16)
-    int (*cur)[32];          // [kRMax][32] each lane's current pixels (slow path only)
+    int (*cur)[32];          // [kRMax][32] each lane's current pixels (read when the footprint moves)
     StagedRec<P>* rec;       // [seg_len]
     static constexpr size_t kFixed = 2 * kRMax * 32 * sizeof(int);
     __device__ explicit WarpSmem(unsigned char* base)
@@ -201,6 +200,8 @@ __device__ __forceinline__ int entry_key(const int4& E) { return E.w; }
 // the first record not processed.  R is warp-uniform.  RT > 0 fixes R = RT at compile time (the
 // point loops then run without per-point checks; points past S^2 in the last block load sample
 // offset 0 and are never flushed); RT = 0 takes the runtime R and stops each loop at it.
+// The samples of a record are loaded just before its FMAs: the other warps on the SM hide
+// their latency (a register prefetch of the next record's samples measured slower).
 template <int P, typename TS, bool COMP, int RT>
 __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R, int blk, int N, int lane,
                                            WarpSmem<P>& sm, const TS* __restrict__ table,
@@ -230,56 +231,37 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
             for (int q = 0; q < KA; ++q) acc[r][p][q] = 0ull;
     }
     int fp = -1;             // footprint origin (x0 | y0 << 16) the offsets refer to
-    bool pre = false;        // the current buffer holds the current record's samples (prefetched)
-    KV kva[kRMax], kvb[kRMax];     // raw samples, widened to float when used
-    // One record: load its samples unless prefetched, prefetch the next record's into `nxt` when
-    // it keeps the footprint, then accumulate.  Returns false when the run ends at record j.
-    auto step = [&](KV (&cur_kv)[kRMax], KV (&nxt)[kRMax]) -> bool {
-        if (j >= e1) return false;
+    for (; j < e1; ++j) {
         const int4 E = sm.rec[j].e;
-        if (entry_key(E) != key) return false;
-        if (!pre) {
-            if (E.x != fp) {     // the footprint moved: new offsets, flush the pixels that change
-                const int x0 = E.x & 0xFFFF, y0 = (E.x >> 16) & 0xFFFF;
-                const int cu = E.y & 0xFFFF, cv = (E.y >> 16) & 0xFFFF;
-#pragma unroll
-                for (int r = 0; r < kRMax; ++r) {
-                    if (r < R && (valid & (1u << r))) {
-                        const int puv = sm.puv[r][lane];
-                        int du = (puv & 0xFFFF) + cu;
-                        du -= (du >= S) ? S : 0;
-                        int dv = (puv >> 16) + cv;
-                        dv -= (dv >= S) ? S : 0;
-                        toff[r] = dv * S + du;
-                        const int pix = (y0 + dv) * N + x0 + du;
-                        const int cur = sm.cur[r][lane];
-                        if (pix != cur) {
-                            if (cur >= 0) flush_pixel<P, COMP>(gch, ech, cur, acc[r]);
-                            sm.cur[r][lane] = pix;
-                        }
-                    }
-                }
-                fp = E.x;
-            }
-            const TS* kz = table + E.z;
+        if (entry_key(E) != key) break;
+        if (E.x != fp) {     // the footprint moved: new offsets, flush the pixels that change
+            const int x0 = E.x & 0xFFFF, y0 = (E.x >> 16) & 0xFFFF;
+            const int cu = E.y & 0xFFFF, cv = (E.y >> 16) & 0xFFFF;
 #pragma unroll
             for (int r = 0; r < kRMax; ++r) {
-                if (RT == 0 && r >= R) break;
-                if (r < R) cur_kv[r] = load_kv(kz + toff[r]);   // invalid points read offset 0, never flushed
-            }
-        }
-        pre = false;
-        if (j + 1 < e1) {
-            const int4 E1 = sm.rec[j + 1].e;
-            if (E1.x == fp && entry_key(E1) == key) {
-                const TS* kz = table + E1.z;
-#pragma unroll
-                for (int r = 0; r < kRMax; ++r) {
-                    if (RT == 0 && r >= R) break;
-                    if (r < R) nxt[r] = load_kv(kz + toff[r]);
+                if (r < R && (valid & (1u << r))) {
+                    const int puv = sm.puv[r][lane];
+                    int du = (puv & 0xFFFF) + cu;
+                    du -= (du >= S) ? S : 0;
+                    int dv = (puv >> 16) + cv;
+                    dv -= (dv >= S) ? S : 0;
+                    toff[r] = dv * S + du;
+                    const int pix = (y0 + dv) * N + x0 + du;
+                    const int cur = sm.cur[r][lane];
+                    if (pix != cur) {
+                        if (cur >= 0) flush_pixel<P, COMP>(gch, ech, cur, acc[r]);
+                        sm.cur[r][lane] = pix;
+                    }
                 }
-                pre = true;
             }
+            fp = E.x;
+        }
+        KV kv[kRMax];
+        const TS* kz = table + E.z;
+#pragma unroll
+        for (int r = 0; r < kRMax; ++r) {
+            if (RT == 0 && r >= R) break;
+            if (r < R) kv[r] = load_kv(kz + toff[r]);   // invalid points read offset 0, never flushed
         }
         if constexpr (KA == 2) {
             // A += k (gx, gx), B += k (gy, gy)
@@ -294,7 +276,7 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
             for (int r = 0; r < kRMax; ++r) {
                 if (RT == 0 && r >= R) break;
                 if (r < R) {
-                    const f32x2 k = kv_x2(cur_kv[r]);
+                    const f32x2 k = kv_x2(kv[r]);
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
                         acc[r][p][0] = fma2(k, gxx[p], acc[r][p][0]);
@@ -315,19 +297,13 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
             for (int r = 0; r < kRMax; ++r) {
                 if (RT == 0 && r >= R) break;
                 if (r < R) {
-                    const float2 kv = unpack2(kv_x2(cur_kv[r]));
-                    const f32x2 kxx = pack2(kv.x, kv.x), kyy = pack2(kv.y, kv.y);
+                    const float2 k = unpack2(kv_x2(kv[r]));
+                    const f32x2 kxx = pack2(k.x, k.x), kyy = pack2(k.y, k.y);
 #pragma unroll
                     for (int p = 0; p < P; ++p) acc[r][p][0] = fma2(g2[p], kyy, fma2(g1[p], kxx, acc[r][p][0]));
                 }
             }
         }
-        ++j;
-        return true;
-    };
-    for (;;) {
-        if (!step(kva, kvb)) break;
-        if (!step(kvb, kva)) break;
     }
 #pragma unroll
     for (int r = 0; r < kRMax; ++r) {
