@@ -151,6 +151,7 @@ struct PlaceParams {
     int qlim;                             // beta (N/2 + 2): |q| beyond it is off the grid
     int beta_log2;                        // log2(beta), or -1 when beta is not a power of two
     int flag_vec;                         // the flag array is aligned to n_pol bytes
+    float kscale_f;                       // (K - 1) / sqrt(w_max): estimate of the nearest plane
 };
 
 int launch_prep(const Table& t, const Grid& g, const wg_vis_in& in, int flags, WorkList& wl,

@@ -167,6 +167,7 @@ __device__ __forceinline__ Placed place(const double* __restrict__ uvw, int64_t 
     Placed o;
     o.info = make_int4(0, 0, 0, rf.neg ? (1 << kBitNeg) : 0);
     o.S = 0;
+    const bool unflagged = any_unflagged(flag, rec, P, pp.flag_vec);   // issued early: its latency overlaps the placement
     int iqu, iqv, k = 0;
     bool fast = false;
     {
@@ -183,13 +184,15 @@ __device__ __forceinline__ Placed place(const double* __restrict__ uvw, int64_t 
             if (!(hi_w < fbK)) {
                 fast = false;            // near or beyond the last bound, infinite or NaN: exact steps
             } else {
-                int lo = 0, hi = pp.K - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (__ldg(&pp.wbounds_f[mid - 1]) < lo_w) lo = mid; else hi = mid - 1;
-                }
-                k = lo;
-                if (k < pp.K - 1 && !(__ldg(&pp.wbounds_f[k]) > hi_w)) fast = false;
+                // the nearest plane in sqrt(w) directly, floor((K-1) sqrt(w / w_max) + 1/2), then
+                // both of its bounds checked with the margin: b_k <= w < b_{k+1} decided, or the
+                // exact steps (an estimate off by one near a bound fails the check)
+                int kk = __float2int_rd(fmaf(pp.kscale_f, sqrtf(wf), 0.5f));
+                kk = min(max(kk, 0), pp.K - 1);
+                if ((kk == 0 || __ldg(&pp.wbounds_f[kk - 1]) < lo_w) && __ldg(&pp.wbounds_f[kk]) > hi_w)
+                    k = kk;
+                else
+                    fast = false;
             }
         }
     }
@@ -203,14 +206,9 @@ __device__ __forceinline__ Placed place(const double* __restrict__ uvw, int64_t 
     const int h = (S - 1) / 2;
     const int x0 = pp.N / 2 + xc - h, y0 = pp.N / 2 + yc - h;
     if (x0 < 0 || y0 < 0 || x0 + S - 1 > pp.N - 1 || y0 + S - 1 > pp.N - 1) return o;
-    if (!any_unflagged(flag, rec, P, pp.flag_vec)) return o;
+    if (!unflagged) return o;
     const int sub = (fv - pp.lo) * pp.beta + (fu - pp.lo);
-    // (-x0) mod S: the residue class of the footprint's first column (x0 >= 0)
-    const float inv_s = __frcp_rn((float)S);
-    const int rx = mod_small(x0, S, inv_s), ry = mod_small(y0, S, inv_s);
-    const int cu = rx ? S - rx : 0, cv = ry ? S - ry : 0;
-    o.info.x = x0 | (y0 << 16);
-    o.info.y = cu | (cv << 16);
+    o.info.x = x0 | (y0 << 16);        // info.y (the footprint's residues) is filled for entries only
     o.info.z = __ldg(&pp.offsets[k]) + sub * S * S;
     o.info.w |= k | (1 << kBitGd);
     o.S = S;
@@ -662,7 +660,11 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
             continue;
         }
         const int ech = pp.wstack ? ch * pp.K + k : gch;   // the grid channel
-        entries[dst] = make_int4(info.x, info.y, info.z, k | (ech << 16));
+        // (-x0) mod S and (-y0) mod S: the residue classes of the footprint's first column and row
+        const float inv_s = __frcp_rn((float)S);
+        const int rx = mod_small(info.x & 0xFFFF, S, inv_s), ry = mod_small((info.x >> 16) & 0xFFFF, S, inv_s);
+        const int cuv = (rx ? S - rx : 0) | ((ry ? S - ry : 0) << 16);
+        entries[dst] = make_int4(info.x, cuv, info.z, k | (ech << 16));
 #pragma unroll
         for (int p = 0; p < P; ++p) gamma[(int64_t)dst * P + p] = acc[p];
         // runs: first and last row of the channel, or first and last record when interleaved
@@ -805,6 +807,7 @@ static PlaceParams place_params(const Table& t, int n, double du, int C, int P, 
         if (t.beta == (1 << b)) pp.beta_log2 = b;
     pp.zeta_f = t.zeta_f;
     pp.flag_vec = 0;
+    pp.kscale_f = (t.K > 1 && t.w_max > 0.0) ? (float)((t.K - 1) / std::sqrt(t.w_max)) : 0.0f;
     return pp;
 }
 
