@@ -11,8 +11,9 @@
 // (all polarisations) in registers and reloads one only when the footprint moves and the class's
 // pixel changes; for consecutive entries of a track that keep the footprint and differ only in
 // the sub-kernel z it loads nothing but the kernel samples.  Per entry each lane sums its R
-// points, the warp reduces the 2P floats by a shuffle reduce-scatter, and 2P lanes add the
-// entry's sums into a per-entry FP32 accumulator (one atomic add per float per footprint block).
+// points into 2P floats; these go through a shared-memory transpose (batches of 64 / (2P)
+// entries), after which each lane holds two components of one entry summed over the warp and
+// adds them to a per-entry FP32 accumulator with one vector atomic per footprint block.
 //
 // k_degrid_out writes the records of each entry's run.  Compression (Sec. 4.3.3) carries over:
 // every record compressed into an entry has its footprint and kernel samples, so m is computed
@@ -72,50 +73,63 @@ __device__ __forceinline__ void load_pixel(const float2* __restrict__ g, f32x2 (
     }
 }
 
-// Per-warp shared memory: the residue-class arrays, then the segment's staged entries.
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// The per-entry reduction buffers 64 / (2P) entries of 2P lane partials: slot b holds lane l's
+// component c at b * (33 * 2P) + l * 2P + c (one 2P-float pad per slot, so that the 32 lanes'
+// reads of two adjacent components of 32 / P different slots fall in distinct banks).
+constexpr int kRedFloats = 64 * 33;      // per warp, any P
+
+// Per-warp shared memory: the residue-class arrays, the reduction buffer, then the segment's
+// staged entries.
 struct WarpSmem {
     int (*puv)[32];          // [kRMax][32] each lane's owned residue classes (pu | pv << 16)
+    float* red;              // [kRedFloats]
     int4* rec;               // [seg_len] entries, w replaced by the key
-    static constexpr size_t kFixed = kRMax * 32 * sizeof(int);
+    static constexpr size_t kFixed = kRMax * 32 * sizeof(int) + kRedFloats * sizeof(float);
     __device__ explicit WarpSmem(unsigned char* base)
         : puv(reinterpret_cast<int (*)[32]>(base)),
+          red(reinterpret_cast<float*>(base + kRMax * 32 * sizeof(int))),
           rec(reinterpret_cast<int4*>(base + kFixed)) {}
     static constexpr size_t bytes(int seg_len) { return kFixed + (size_t)seg_len * sizeof(int4); }
 };
 
-// Sums v[0..V) over the warp and scatters the sums: lane l returns the total of component
-// l / (32 / V).  log2(V) halving exchanges (each lane sends the half it does not keep), then
-// xor-butterflies over the remaining lane bits.
-template <int V>
-__device__ __forceinline__ float warp_reduce_scatter(float (&v)[V], int lane)
-{
-#pragma unroll
-    for (int h = V / 2, m = 16; h >= 1; h >>= 1, m >>= 1) {
-        const bool up = (lane & m) != 0;
-#pragma unroll
-        for (int i = 0; i < h; ++i) {
-            const float send = up ? v[i] : v[i + h];
-            const float keep = up ? v[i + h] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
-        }
-    }
-    float s = v[0];
-#pragma unroll
-    for (int m = 16 / V; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-    return s;
-}
-
 // Entries [j, e1) of the staged segment while their key (support, grid channel) equals `key`,
 // footprint block `blk`, R points per lane (RT > 0 fixes R at compile time; points past S^2
 // keep pixel value 0 and read sample offset 0).  Adds each entry's sums to acc[j][2P]; returns
-// the first entry not processed.
+// the first entry not processed.  Each lane stores its 2P partials of an entry in the reduction
+// buffer; every 64 / (2P) entries (and at the end) each lane sums two adjacent components of one
+// entry over the 32 lanes and adds them to acc with one vector atomic.
 template <int P, int RT>
 __device__ __forceinline__ int degrid_records(int j, int e1, int key, int S, int R, int blk, int N, int lane,
                                               WarpSmem& sm, const float2* __restrict__ table,
                                               const float2* __restrict__ gch, float* __restrict__ acc)
 {
-    constexpr int V = 2 * P;
+    constexpr int V = 2 * P, NB = 64 / V, SLOT = 33 * V;
     if constexpr (RT > 0) R = RT;
+    int nbuf = 0, jb = j;     // entries buffered, and the first of them
+    // lane l sums components c, c + 1 of buffered entry b over the 32 lanes
+    auto drain = [&](int n) {
+        __syncwarp();
+        const int b = (2 * lane) / V, c = (2 * lane) % V;
+        if (b < n) {
+            const float* src = sm.red + b * SLOT + c;
+            f32x2 t = 0ull;
+#pragma unroll
+            for (int l2 = 0; l2 < 32; ++l2) {
+                // V = 8: lanes with bit 2 set stored their two 16-byte halves swapped
+                const int cs = (V == 8 && (l2 & 4)) ? 4 : 0;
+                t = add2(t, *reinterpret_cast<const f32x2*>(src + l2 * V + (c ^ cs) - c));
+            }
+            atomicAdd(reinterpret_cast<float2*>(acc + (size_t)(jb + b) * V + c), unpack2(t));
+        }
+        __syncwarp();
+    };
     f32x2 pv[kRMax][P];
     int toff[kRMax], cur[kRMax];     // sample offset and pixel held of each owned class
     unsigned valid = 0;
@@ -189,9 +203,25 @@ __device__ __forceinline__ int degrid_records(int j, int e1, int key, int S, int
             v[2 * p] = a.x + b.y;
             v[2 * p + 1] = a.y - b.x;
         }
-        const float sum = warp_reduce_scatter<V>(v, lane);
-        if ((lane & (32 / V - 1)) == 0) atomicAdd(acc + (size_t)j * V + lane / (32 / V), sum);
+        float* dst = sm.red + nbuf * SLOT + lane * V;
+        if constexpr (V == 8) {
+            // halves swapped for lanes with bit 2 set: the 8 lanes of a quarter-warp store to
+            // distinct banks
+            const int sw = (lane & 4) ? 4 : 0;
+            *reinterpret_cast<float4*>(dst + sw) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4*>(dst + (4 ^ sw)) = make_float4(v[4], v[5], v[6], v[7]);
+        } else if constexpr (V == 4) {
+            *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+            *reinterpret_cast<float2*>(dst) = make_float2(v[0], v[1]);
+        }
+        if (++nbuf == NB) {
+            drain(NB);
+            nbuf = 0;
+            jb = j + 1;
+        }
     }
+    if (nbuf) drain(nbuf);
     return j;
 }
 
