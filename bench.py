@@ -443,6 +443,19 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     ms_e2e = x0.elapsed_time(x1) / ne
     ms_e2e = max_over_ranks(ms_e2e, world, dev)
+    # the host-to-device copies alone (the link's share of the end-to-end step)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(cstream)
+    for k in range(3):
+        u, b = slots[k % 2]
+        with torch.cuda.stream(cstream):
+            u.copy_(h_uvw, non_blocking=True)
+            b.vis.copy_(h_vis, non_blocking=True)
+            b.weight.copy_(h_w, non_blocking=True)
+            b.flag.copy_(h_f, non_blocking=True)
+    c1.record(cstream)
+    torch.cuda.synchronize()
+    ms_h2d = c0.elapsed_time(c1) / 3
 
     peaks, src = _peaks()
     props = torch.cuda.get_device_properties(local_rank)
@@ -492,6 +505,7 @@ def run_ours(args, rank, world, local_rank):
         "variants": variants,
         "e2e": {"value": round(whole_job_rate(total, ms_e2e, world), 3), "unit": "G grid-point updates/s",
                 "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "h2d_alone_ms": round(ms_h2d, 3), "h2d_gbs": round(h2d / (ms_h2d * 1e-3) / 1e9, 1),
                 "pipelining": "inputs double-buffered on a copy stream"},
         "gpu_launches": int(launches),
         "clocks": clk,

@@ -15,11 +15,12 @@
 // entries), after which each lane holds two components of one entry summed over the warp and
 // adds them to a per-entry FP32 accumulator with one vector atomic per footprint block.
 //
-// k_degrid_out writes the records of each entry's run.  Compression (Sec. 4.3.3) carries over:
+// k_degrid_tile writes the records of each entry's run.  Compression (Sec. 4.3.3) carries over:
 // every record compressed into an entry has its footprint and kernel samples, so m is computed
 // once per entry and written to each record of the run, conjugated back where psi = -1 (w' < 0),
 // with the cross hands swapped back under cross-hand swapping, and for the adjoint mode scaled
-// by eps (1 - f) (the vis -> grid map's R-linear outer factor).
+// by eps (1 - f) (the vis -> grid map's R-linear outer factor).  It works per preparation tile
+// through shared memory so that the output is written row-major with coalesced stores.
 #include "internal.cuh"
 
 namespace wg {
@@ -27,6 +28,8 @@ namespace wg {
 namespace {
 
 constexpr int kWarps = 4;           // warps per block of k_degrid_sum
+constexpr int kTileCap = 4096;      // records per preparation tile: rpb x C <= max(kTileRecords, n_chan <= 4096)
+static_assert(kTileRecords <= kTileCap, "a preparation tile must fit the degridder's output tile");
 
 typedef unsigned long long f32x2;   // a packed FP32 pair (Blackwell f32x2 arithmetic)
 
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_degrid_sum(const int4* __res
                                                                const float2* __restrict__ grid, int N, int K, int C,
                                                                int64_t n_samples, int seg_len, int slots,
                                                                unsigned int* __restrict__ counter,
-                                                               float* __restrict__ acc)
+                                                               float* __restrict__ acc, long long* __restrict__ dropped)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -287,9 +290,9 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_degrid_sum(const int4* __res
         __syncwarp();
         for (int i = lane; i < n; i += 32) {
             const int4 E = sm.rec[i];
-            sm.rec[i].w = entry_ok(E, supports, N, K, C, n_samples)
-                              ? (__ldg(&supports[E.w & 0xFFF]) << 16) | ((E.w >> 16) & 0xFFFF)
-                              : -1;
+            const bool ok = entry_ok(E, supports, N, K, C, n_samples);
+            sm.rec[i].w = ok ? (__ldg(&supports[E.w & 0xFFF]) << 16) | ((E.w >> 16) & 0xFFFF) : -1;
+            if (!ok && blk == 0) atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
         }
         __syncwarp();
 
@@ -316,56 +319,77 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_degrid_sum(const int4* __res
 
 // One thread per entry writes the records of its run: rows run.x..run.y of input channel
 // gchan / kst (w-stacking: kst planes per channel), or records run.x..run.y when interleaved.
+// One block per preparation tile (rpb rows x all channels) writes the tile's output records
+// row-major.  Phase 1 puts each entry's sums into the shared-memory tile at the records of its
+// run that fall in the tile (the run before the tile's first head of a list can reach into
+// it), phase 2 stores the tile with coalesced vector stores, conjugated back where psi = -1
+// (the take-conjugate class bit), with the cross hands swapped back under cross-hand swapping,
+// and for the adjoint mode scaled by eps (1 - f).  Records that are not griddable are in no run
+// and keep the tile's zero.  Lists: one per input channel (rows), or one in natural record
+// order when interleaved.
 template <int P>
-__global__ void k_degrid_out(const int4* __restrict__ entries, const int2* __restrict__ runs,
-                             const long long* __restrict__ scal, const int* __restrict__ supports,
-                             const float2* __restrict__ acc, int N, int K, int Cg, int C, int kst, int64_t n_samples,
-                             const double* __restrict__ uvw, const float* __restrict__ weight,
-                             const uint8_t* __restrict__ flag, int adjoint, float2* __restrict__ out, int64_t rows,
-                             int interleave, int cross_swap, long long* __restrict__ dropped)
+__global__ void __launch_bounds__(512) k_degrid_tile(const int2* __restrict__ runs, const float2* __restrict__ acc,
+                                                     const int* __restrict__ tile_off, const int* __restrict__ chan_base,
+                                                     const uint8_t* __restrict__ rclass, const float* __restrict__ weight,
+                                                     const uint8_t* __restrict__ flag, int adjoint, int cross_swap,
+                                                     int interleave, int64_t rows, int rpb, int C, int64_t n_tiles,
+                                                     float2* __restrict__ out)
 {
-    const long long n = scal[0];
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int4 E = entries[e];
-        const int2 run = runs[e];
-        const int ch = ((E.w >> 16) & 0xFFFF) / kst;
-        if (!entry_ok(E, supports, N, K, Cg, n_samples) || ch >= C || run.x < 0 || run.y < run.x ||
-            (int64_t)run.y >= (interleave ? rows * C : rows)) {
-            atomicAdd(reinterpret_cast<unsigned long long*>(dropped), 1ull);
-            continue;
+    extern __shared__ __align__(16) float2 s_out[];      // [rpb * C][P]
+    const int64_t tile = blockIdx.x;
+    const int64_t row0 = tile * rpb;
+    const int nrows = (int)min((int64_t)rpb, rows - row0);
+    const int nrec = nrows * C;
+    for (int i = threadIdx.x; i < nrec * P; i += blockDim.x) s_out[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int nlist = interleave ? 1 : C;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // the tile in list units: rows of a channel, or records in natural order
+    const int64_t lo = interleave ? row0 * C : row0, hi = interleave ? row0 * C + nrec : row0 + nrows;
+    for (int l = threadIdx.x >> 5; l < nlist; l += nw) {
+        const int base = chan_base[l];
+        const int first = base + tile_off[tile * C + l];
+        const int end = tile + 1 < n_tiles ? base + tile_off[(tile + 1) * C + l] : chan_base[l + 1];
+        for (int e = first - 1 + lane; e < end; e += 32) {
+            if (e < base) continue;
+            const int2 run = runs[e];
+            const int64_t a = max((int64_t)run.x, lo), b = min((int64_t)run.y + 1, hi);
+            if (a >= b) continue;
+            float2 m[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) m[p] = acc[(int64_t)e * P + p];
+            for (int64_t r = a; r < b; ++r) {
+                const int j = interleave ? (int)(r - lo) : (int)(r - row0) * C + l;
+#pragma unroll
+                for (int p = 0; p < P; ++p) s_out[j * P + p] = m[p];
+            }
         }
-        float2 m[P];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
+        const int64_t rec = row0 * C + j;
+        const bool neg = (rclass[rec] >> 3) & 1;
+        float2 v[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) m[p] = acc[e * P + p];
-        for (int r = run.x; r <= run.y; ++r) {
-            const int64_t rec = interleave ? (int64_t)r : (int64_t)r * C + ch;
-            const int64_t row = interleave ? (int64_t)r / C : (int64_t)r;
-            const bool neg = uvw[3 * row + 2] < 0.0;
-            float2 v[P];
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                // with cross-hand swapping, output pol 1 of a take-conjugate record comes from
-                // grid pol 2 and pol 2 from pol 1 (the adjoint of the swap is the swap)
-                float2 a = m[p];
-                if constexpr (P == 4) {
-                    if (cross_swap && neg && p == 1) a = m[2];
-                    if (cross_swap && neg && p == 2) a = m[1];
-                }
-                v[p] = neg ? make_float2(a.x, -a.y) : a;
-                if (adjoint) {
-                    const float wf = weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
-                    v[p].x *= wf;
-                    v[p].y *= wf;
-                }
+        for (int p = 0; p < P; ++p) {
+            // with cross-hand swapping, output pol 1 of a take-conjugate record comes from grid
+            // pol 2 and pol 2 from pol 1 (the adjoint of the swap is the swap)
+            const int src = (P == 4 && cross_swap && neg && (p == 1 || p == 2)) ? 3 - p : p;
+            const float2 a = s_out[j * P + src];
+            v[p] = neg ? make_float2(a.x, -a.y) : a;
+            if (adjoint) {
+                const float wf = weight[rec * P + p] * (1.0f - (float)flag[rec * P + p]);
+                v[p].x *= wf;
+                v[p].y *= wf;
             }
-            float2* o = out + rec * P;
-            if constexpr (P == 1) {
-                o[0] = v[0];
-            } else {
+        }
+        float2* o = out + rec * P;
+        if constexpr (P == 1) {
+            o[0] = v[0];
+        } else {
 #pragma unroll
-                for (int h = 0; h < P; h += 2)
-                    *reinterpret_cast<float4*>(o + h) = make_float4(v[h].x, v[h].y, v[h + 1].x, v[h + 1].y);
-            }
+            for (int h = 0; h < P; h += 2)
+                *reinterpret_cast<float4*>(o + h) = make_float4(v[h].x, v[h].y, v[h + 1].x, v[h + 1].y);
         }
     }
 }
@@ -386,7 +410,7 @@ static int degrid_sum_launch(const Grid& g, const Table& t, const WorkList& wl, 
     }
     k_degrid_sum<P, RT><<<num_sms() * bps, kWarps * 32, smem, s>>>(
         wl.entries, wl.seg_off, wl.scal, t.supports_d, t.data, g.data, g.n, t.K, g.n_chan, t.n_samples, wl.seg_len,
-        wl.slots, wl.task_counter + 1, reinterpret_cast<float*>(wl.dacc));
+        wl.slots, wl.task_counter + 1, reinterpret_cast<float*>(wl.dacc), wl.scal + 3);
     WG_LAUNCHED("k_degrid_sum");
     return WG_OK;
 }
@@ -396,7 +420,6 @@ static int degrid_impl(const Grid& g, const Table& t, const wg_vis_in& in, const
                        cudaStream_t s)
 {
     if (!wl.dacc) return fail(WG_E_INVALID_ARG, "degrid_vis: the work list has no degridding accumulator");
-    WG_CUDA(cudaMemsetAsync(out, 0, sizeof(float2) * (size_t)in.n_rows * in.n_chan * P, s));
     WG_CUDA(cudaMemsetAsync(wl.task_counter + 1, 0, sizeof(unsigned int), s));
     const int zb = num_sms() * 4;
     k_degrid_zero<<<zb, 256, 0, s>>>(reinterpret_cast<float4*>(wl.dacc), wl.scal, P);
@@ -406,11 +429,20 @@ static int degrid_impl(const Grid& g, const Table& t, const wg_vis_in& in, const
     else if (wl.fixed_r && wl.slots == 128) rc = degrid_sum_launch<P, 4>(g, t, wl, s);
     else rc = degrid_sum_launch<P, 0>(g, t, wl, s);
     if (rc != WG_OK) return rc;
-    k_degrid_out<P><<<num_sms() * 8, 256, 0, s>>>(wl.entries, wl.runs, wl.scal, t.supports_d, wl.dacc, g.n, t.K,
-                                                  g.n_chan, in.n_chan, wl.wstack_k, t.n_samples, in.uvw, in.weight,
-                                                  in.flag, mode == WG_DEGRID_ADJOINT ? 1 : 0, out, in.n_rows,
-                                                  wl.interleave ? 1 : 0, wl.cross_swap ? 1 : 0, wl.scal + 3);
-    WG_LAUNCHED("k_degrid_out");
+    const int tile_smem = (int)(sizeof(float2) * (size_t)wl.rpb * in.n_chan * P);
+    static bool attr_set[5] = {false, false, false, false, false};
+    if (!attr_set[P]) {
+        WG_CUDA(cudaFuncSetAttribute(k_degrid_tile<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(float2) * (size_t)kTileCap * P)));
+        attr_set[P] = true;
+    }
+    if (tile_smem > (int)(sizeof(float2) * (size_t)kTileCap * P))
+        return fail(WG_E_CAPACITY, "degrid_vis: %d records per preparation tile exceed %d", wl.rpb * in.n_chan, kTileCap);
+    if (wl.n_tiles == 0) return WG_OK;     // no records
+    k_degrid_tile<P><<<(unsigned)wl.n_tiles, 512, tile_smem, s>>>(
+        wl.runs, wl.dacc, wl.tile_cnt, wl.chan_base, wl.rclass, in.weight, in.flag, mode == WG_DEGRID_ADJOINT ? 1 : 0,
+        wl.cross_swap ? 1 : 0, wl.interleave ? 1 : 0, in.n_rows, wl.rpb, in.n_chan, wl.n_tiles, out);
+    WG_LAUNCHED("k_degrid_tile");
     return WG_OK;
 }
 
