@@ -95,11 +95,9 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
 }
 
 // kernel-table samples: complex float32, bfloat16 or float16, widened to float at use
-__device__ __forceinline__ float2 to_f2(float2 v) { return v; }
 __device__ __forceinline__ float2 to_f2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
 __device__ __forceinline__ float2 to_f2(__half2 v) { return __half22float2(v); }
 
-__device__ __forceinline__ float2 load_sample(const float2* p) { return __ldg(p); }
 template <typename TS>
 __device__ __forceinline__ TS load_sample(const TS* p)
 {
@@ -446,18 +444,26 @@ static int grid_launch(Grid& g, const Table& t, const WorkList& wl, const TS* ta
     return WG_OK;
 }
 
-// The fixed-R kernels exist for FP32 tables without compensation, slots = 128 or 256.
+// Fixed-R kernels: R = 8 (slots = 256) for every table type, with or without compensation;
+// R = 4 (slots = 128) for FP32 tables without compensation.  Other plans take the runtime-R
+// kernel.
 template <int P, bool COMP>
 static int grid_dispatch(Grid& g, const Table& t, const WorkList& wl, cudaStream_t s)
 {
+    const bool r8 = wl.fixed_r && wl.slots == 256;
     switch (t.store) {
-        case WG_BF16:
-            return grid_launch<P, __nv_bfloat162, COMP, 0>(g, t, wl, static_cast<const __nv_bfloat162*>(t.data_lp), s);
-        case WG_F16:
-            return grid_launch<P, __half2, COMP, 0>(g, t, wl, static_cast<const __half2*>(t.data_lp), s);
+        case WG_BF16: {
+            const auto* tb = static_cast<const __nv_bfloat162*>(t.data_lp);
+            return r8 ? grid_launch<P, __nv_bfloat162, COMP, 8>(g, t, wl, tb, s)
+                      : grid_launch<P, __nv_bfloat162, COMP, 0>(g, t, wl, tb, s);
+        }
+        case WG_F16: {
+            const auto* th = static_cast<const __half2*>(t.data_lp);
+            return r8 ? grid_launch<P, __half2, COMP, 8>(g, t, wl, th, s) : grid_launch<P, __half2, COMP, 0>(g, t, wl, th, s);
+        }
         default:
+            if (r8) return grid_launch<P, float2, COMP, 8>(g, t, wl, t.data, s);
             if constexpr (!COMP) {
-                if (wl.fixed_r && wl.slots == 256) return grid_launch<P, float2, false, 8>(g, t, wl, t.data, s);
                 if (wl.fixed_r && wl.slots == 128) return grid_launch<P, float2, false, 4>(g, t, wl, t.data, s);
             }
             return grid_launch<P, float2, COMP, 0>(g, t, wl, t.data, s);

@@ -28,7 +28,7 @@ VARIANTS = [  # name, table storage, half visibilities, compensated flush, rel-L
 ]
 
 
-def _grid(wl, store, half, comp):
+def _grid(wl, store, half, comp, plan=None):
     dev = "cuda"
     t = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports,
                            store=store)
@@ -42,6 +42,8 @@ def _grid(wl, store, half, comp):
                             wl.vis.to(dev), wl.weight.to(dev), wl.flag.to(dev))
     wlst = wg.WorkList(wl.rows * wl.n_chan, wl.n_chan, wl.n_pol)
     wg.vis_compress(g, t, batch, wlst)
+    if plan is not None:
+        wlst.plan(t, *plan)
     wg.grid_vis(g, t, wlst)
     torch.cuda.synchronize()
     assert wlst.stats()["dropped"] == 0
@@ -72,3 +74,13 @@ def test_low_precision_table_is_round_to_nearest(store, dtype):
     ref = torch.view_as_real(torch.as_tensor(data)).to(dtype)               # torch's RNE conversion
     got = t.lp_samples().cpu().view(dtype).reshape(-1, 2)
     assert torch.equal(got.view(torch.int16), ref.view(torch.int16))
+
+
+@pytest.mark.parametrize("name,store,half,comp,bar", VARIANTS)
+def test_precision_variants_fixed_r(name, store, half, comp, bar):
+    # the same bars under the fixed R = 8 plan, which every table type and the compensated
+    # flush run with their own kernel
+    wl = synth.make("wproj_2k", n_times=24, n_chan=2, n_baselines=300, flag_frac=0.01)
+    ref = run_oracle(wl)["grid"]
+    got = _grid(wl, store, half, comp, plan=(256, 256, True))
+    assert rel_l2(got, ref) < bar and max_rel(got, ref) < bar * 10, name
