@@ -310,6 +310,104 @@ def run_ours(args, rank, world, local_rank):
     total = st["updates"] + st["updates_saved"]
     value = whole_job_rate(total, ms, world)
 
+    # end to end: every step copies its inputs from pinned host memory and reads its Stokes-I
+    # image back.  The copies of step k+1 run on a copy stream into the other of two device
+    # input buffers while step k computes (double buffering).  Measured right after the
+    # device-timed steps, over as many steps.
+    h_uvw = torch.as_tensor(wl.uvw).pin_memory()
+    h_vis = wl.vis.cpu().pin_memory()
+    h_w = wl.weight.cpu().pin_memory()
+    h_f = wl.flag.cpu().pin_memory()
+    h_img = torch.empty(img.shape, dtype=img.dtype).pin_memory()
+    h2d = h_uvw.numel() * 8 + h_vis.numel() * 8 + h_w.numel() * 4 + h_f.numel() + freq_d.numel() * 8
+    d2h = h_img.numel() * 4
+    slots = []
+    for _ in range(2):
+        u = torch.empty_like(uvw_d)
+        slots.append((u, wg.VisBatch(u, freq_d, torch.empty_like(wl.vis), torch.empty_like(wl.weight),
+                                     torch.empty_like(wl.flag))))
+    cstream = torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+    ne = max(3, args.steps)
+    # per-step copy and compute intervals, for the share of the copies hidden under compute
+    tl_c = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ne)]
+    tl_s = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ne)]
+
+    def issue_copy(k, tl):
+        u, b = slots[k % 2]
+        with torch.cuda.stream(cstream):
+            cstream.wait_event(consumed[k % 2])
+            if tl:
+                tl_c[k][0].record(cstream)
+            u.copy_(h_uvw, non_blocking=True)
+            b.vis.copy_(h_vis, non_blocking=True)
+            b.weight.copy_(h_w, non_blocking=True)
+            b.flag.copy_(h_f, non_blocking=True)
+            if tl:
+                tl_c[k][1].record(cstream)
+            copied[k % 2].record(cstream)
+
+    def e2e_run(n, tl=False):
+        for k in range(2):
+            consumed[k].record(stream)
+        issue_copy(0, tl)
+        for k in range(n):
+            if k + 1 < n:
+                issue_copy(k + 1, tl)
+            stream.wait_event(copied[k % 2])
+            if tl:
+                tl_s[k][0].record(stream)
+            b = slots[k % 2][1]
+            g.zero()
+            wg.vis_compress(g, tab, b, wlst, compress=compress, interleave=inter, wstack=bool(stack_k))
+            wg.grid_vis(g, tab, wlst)
+            wg.grid_correct(g, tab, mode=img_mode, out=img)
+            consumed[k % 2].record(stream)
+            h_img.copy_(img, non_blocking=True)
+            if tl:
+                tl_s[k][1].record(stream)
+
+    e2e_run(2)
+    torch.cuda.synchronize()
+    barrier(world)
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x0.record(stream)
+    e2e_run(ne, tl=True)
+    x1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = x0.elapsed_time(x1) / ne
+    ms_e2e = max_over_ranks(ms_e2e, world, dev)
+    # copy k+1 against step k: the share of the copy time that ran under compute
+    hid = tot = 0.0
+    for k in range(ne - 1):
+        c0, c1 = x0.elapsed_time(tl_c[k + 1][0]), x0.elapsed_time(tl_c[k + 1][1])
+        s0, s1 = x0.elapsed_time(tl_s[k][0]), x0.elapsed_time(tl_s[k][1])
+        tot += c1 - c0
+        hid += max(0.0, min(c1, s1) - max(c0, s0))
+    copy_hidden = hid / tot if tot > 0 else None
+    # the host-to-device copies alone (the link's share of the end-to-end step)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(cstream)
+    for k in range(3):
+        u, b = slots[k % 2]
+        with torch.cuda.stream(cstream):
+            u.copy_(h_uvw, non_blocking=True)
+            b.vis.copy_(h_vis, non_blocking=True)
+            b.weight.copy_(h_w, non_blocking=True)
+            b.flag.copy_(h_f, non_blocking=True)
+    c1.record(cstream)
+    torch.cuda.synchronize()
+    ms_h2d = c0.elapsed_time(c1) / 3
+    e2e = {"value": round(whole_job_rate(total, ms_e2e, world), 3), "unit": "G grid-point updates/s",
+           "ms_per_step": round(ms_e2e, 3), "steps": ne, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "h2d_alone_ms": round(ms_h2d, 3),
+           "h2d_gbs": round(h2d / (ms_h2d * 1e-3) / 1e9, 1),
+           "copy_hidden_frac": None if copy_hidden is None else round(copy_hidden, 3),
+           "pipelining": "inputs double-buffered on a copy stream"}
+    del slots, h_uvw, h_vis, h_w, h_f, h_img
+    torch.cuda.synchronize()
+
     # precision variants (reduced-precision tables, half visibilities, compensated flushes)
     variants = {}
     if not args.no_variants and not inter and not stack_k:
@@ -387,76 +485,6 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t_degrid = d0.elapsed_time(d1) / nd
 
-    # end to end: every step copies its inputs from pinned host memory and reads its Stokes-I
-    # image back.  The copies of step k+1 run on a copy stream into the other of two device
-    # input buffers while step k computes (double buffering).
-    h_uvw = torch.as_tensor(wl.uvw).pin_memory()
-    h_vis = wl.vis.cpu().pin_memory()
-    h_w = wl.weight.cpu().pin_memory()
-    h_f = wl.flag.cpu().pin_memory()
-    h_img = torch.empty(img.shape, dtype=img.dtype).pin_memory()
-    h2d = h_uvw.numel() * 8 + h_vis.numel() * 8 + h_w.numel() * 4 + h_f.numel() + freq_d.numel() * 8
-    d2h = h_img.numel() * 4
-    slots = []
-    for _ in range(2):
-        u = torch.empty_like(uvw_d)
-        slots.append((u, wg.VisBatch(u, freq_d, torch.empty_like(wl.vis), torch.empty_like(wl.weight),
-                                     torch.empty_like(wl.flag))))
-    cstream = torch.cuda.Stream()
-    copied = [torch.cuda.Event() for _ in range(2)]
-    consumed = [torch.cuda.Event() for _ in range(2)]
-
-    def issue_copy(k):
-        u, b = slots[k % 2]
-        with torch.cuda.stream(cstream):
-            cstream.wait_event(consumed[k % 2])
-            u.copy_(h_uvw, non_blocking=True)
-            b.vis.copy_(h_vis, non_blocking=True)
-            b.weight.copy_(h_w, non_blocking=True)
-            b.flag.copy_(h_f, non_blocking=True)
-            copied[k % 2].record(cstream)
-
-    def e2e_run(n):
-        for k in range(2):
-            consumed[k].record(stream)
-        issue_copy(0)
-        for k in range(n):
-            if k + 1 < n:
-                issue_copy(k + 1)
-            stream.wait_event(copied[k % 2])
-            b = slots[k % 2][1]
-            g.zero()
-            wg.vis_compress(g, tab, b, wlst, compress=compress, interleave=inter, wstack=bool(stack_k))
-            wg.grid_vis(g, tab, wlst)
-            wg.grid_correct(g, tab, mode=img_mode, out=img)
-            consumed[k % 2].record(stream)
-            h_img.copy_(img, non_blocking=True)
-
-    e2e_run(2)
-    torch.cuda.synchronize()
-    barrier(world)
-    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ne = max(3, args.steps // 2)
-    x0.record(stream)
-    e2e_run(ne)
-    x1.record(stream)
-    torch.cuda.synchronize()
-    ms_e2e = x0.elapsed_time(x1) / ne
-    ms_e2e = max_over_ranks(ms_e2e, world, dev)
-    # the host-to-device copies alone (the link's share of the end-to-end step)
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    c0.record(cstream)
-    for k in range(3):
-        u, b = slots[k % 2]
-        with torch.cuda.stream(cstream):
-            u.copy_(h_uvw, non_blocking=True)
-            b.vis.copy_(h_vis, non_blocking=True)
-            b.weight.copy_(h_w, non_blocking=True)
-            b.flag.copy_(h_f, non_blocking=True)
-    c1.record(cstream)
-    torch.cuda.synchronize()
-    ms_h2d = c0.elapsed_time(c1) / 3
-
     peaks, src = _peaks()
     props = torch.cuda.get_device_properties(local_rank)
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -503,10 +531,7 @@ def run_ours(args, rank, world, local_rank):
                      "traffic": traffic},
         "ceilings": measured_ceilings(real / (t_grid * 1e-3), wl.n_pol),
         "variants": variants,
-        "e2e": {"value": round(whole_job_rate(total, ms_e2e, world), 3), "unit": "G grid-point updates/s",
-                "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "h2d_alone_ms": round(ms_h2d, 3), "h2d_gbs": round(h2d / (ms_h2d * 1e-3) / 1e9, 1),
-                "pipelining": "inputs double-buffered on a copy stream"},
+        "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,
     }
