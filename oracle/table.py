@@ -14,7 +14,7 @@ Per w-plane k (w_k = w_max (k/(K-1))^2, square-root spacing, Sec. 2.2.1 / 4.2.1)
      (dv, du) (output C-1, Sec. 4.2.2), plane offsets and supports (C-2);
   6. zeta = sum of the real parts of each sub-kernel (eq. "sum", output C-3).
 
-Readings: the patch sample at eta = -1 (which has no +1 partner) is zero
+Readings of passages the thesis leaves open: the patch sample at eta = -1 (which has no +1 partner) is zero
 so that the w = 0 kernel is exactly real and symmetric; screen samples outside the unit
 disk (l^2 + m^2 >= 1) are zero; n - 1 is evaluated as -r^2 / (1 + sqrt(1 - r^2)).
 """

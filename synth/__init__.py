@@ -138,7 +138,7 @@ def visibilities(uvw_m: np.ndarray, freq_hz: np.ndarray, sky: Sky, n_pol: int,
 
 
 # ----------------------------------------------------------------------------------
-# workload descriptions (shapes of the thesis's experiments)
+# workload descriptions (shapes of the thesis's experiments on its LOFAR data sets)
 # ----------------------------------------------------------------------------------
 @dataclasses.dataclass
 class Workload:

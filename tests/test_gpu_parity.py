@@ -1,6 +1,6 @@
 """GPU parity of the whole preparation + gridding path against the FP64 oracle, through the C ABI.
 
-Bars (written here, derived in the design doc):
+Bars (written here; FP32 accumulation against FP64 rounds each add to 2^-24 relative):
   * integer/index work bit-exact: per-record class bits (g, c, griddable), gridded entries
     (footprint origin, kernel pointer, plane, channel), run bounds, statistics;
   * FP32 accumulation vs FP64: grid rel-L2 <= 1e-5 and max-abs <= 1e-5 max|grid|; gamma and

@@ -5,7 +5,7 @@ The oracle grids the original complex64 visibilities with its FP64 table, so eac
 error includes its own storage rounding.  Bars follow the storage precision: FP32 paths 1e-5
 (rel-L2 and max-abs/max|grid|); FP16 tables or visibilities (11-bit significands, relative
 rounding 2^-11 per value) 2e-3; BF16 tables (8-bit significands, 2^-8) 1e-2.  The measured errors
-are printed (run with -s) and recorded in the design doc.
+are printed (run with -s).
 """
 import numpy as np
 import pytest
