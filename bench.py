@@ -363,8 +363,10 @@ def run_ours(args, rank, world, local_rank):
             wg.vis_compress(g, tab, b, wlst, compress=compress, interleave=inter, wstack=bool(stack_k))
             wg.grid_vis(g, tab, wlst)
             wg.grid_correct(g, tab, mode=img_mode, out=img)
-            consumed[k % 2].record(stream)
+            # the slot is released after the image read-back is queued, so the next
+            # host-to-device copy cannot take the link ahead of it and hold up step k+1
             h_img.copy_(img, non_blocking=True)
+            consumed[k % 2].record(stream)
             if tl:
                 tl_s[k][1].record(stream)
 
