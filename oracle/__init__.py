@@ -26,9 +26,11 @@ steps of its Algorithm "convgen" in order, in FP64:
                       chi^2 gradient (not in the thesis)
 
 Parity pins (tests/test_oracle_*.py) tie each of these to something other than itself:
-closed forms, brute force, invariants and worked counts from the thesis.  Parity
-unpinned: absolute kernel values for the exact (non-paraxial) w-screen at large w
-beyond brute-force sizes -- the thesis prints no kernel values.
+closed forms, brute force, invariants and worked counts from the thesis.  Kernel values
+for the exact (non-paraxial) w-screen are pinned by direct 2-D Fourier sums: on whole tables
+for small patches, and on sampled values of the w-projection workload's 256^2-patch table
+up to its w_max.  Tables on larger patches (the 8192^2 workload's 512^2) are not sampled;
+they run the same steps.  The thesis prints no kernel values.
 """
 from .cloops import lib  # noqa: F401  (compiles oracle.c on first use)
 from .pswf import psi0

@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 from oracle.pswf import bandwidth
-from oracle.table import exact_screen
+from oracle.table import default_nk, exact_screen
 
 
 def _offsets(beta, S, fv, fu):
@@ -75,6 +75,42 @@ def test_brute_force_dft_exact_screen(w):
                     u, v = ou[j] * du / beta, ov[i] * du / beta
                     ref = np.sum(f * scr * np.exp(-2j * np.pi * (u * L + v * M))) / norm
                     assert abs(got[i, j] - ref) < 1e-12
+
+
+def test_brute_force_samples_at_full_size():
+    # The w-projection workload's own table: 32 planes up to its w_max, supports 9..65,
+    # beta = 8, 256^2 image patch zero-padded to 2048^2.  Sampled values of the outermost and
+    # a middle plane against direct 2-D Fourier sums over the patch (65536 terms each), which
+    # share none of the oracle's FFT, padding, shift, normalisation or trim steps.
+    import synth
+    wl = synth.make("wproj_2k", n_chan=1, n_times=2, n_baselines=4)   # the full workload's du and w_max
+    n_k = default_nk(max(wl.supports))                 # the patch the workload's table is built on
+    tab = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+    beta, du = tab.beta, wl.du
+    assert (n_k, beta, wl.n_wplanes) == (256, 8, 32)
+    c = bandwidth(wl.taper_support)
+    idx = np.arange(n_k)
+    eta = 2.0 * (idx - n_k // 2) / n_k
+    l = eta / (2 * du)
+    t = np.where(idx == 0, 0.0, oracle.psi0(c, eta))
+    L, M = np.meshgrid(l, l, indexing="xy")
+    f = t[:, None] * t[None, :]
+    norm = f.sum()
+    checked = 0
+    for k in (16, 31):
+        S = int(tab.supports[k])
+        h = (S - 1) // 2
+        scr = f * exact_screen(tab.w_planes[k], L, M)
+        for fv, fu in ((tab.lo, tab.lo + beta - 1), (0, 0), (2, -1)):
+            ov, ou = _offsets(beta, S, fv, fu)
+            got = tab.sub_kernel(k, fv, fu)
+            for i, j in ((h, h), (h, 0), (0, h), (h // 2, h + 3), (S - 1, S - 2)):
+                u, v = ou[j] * du / beta, ov[i] * du / beta
+                ref = np.sum(scr * np.exp(-2j * np.pi * (u * L + v * M))) / norm
+                assert abs(got[i, j] - ref) < 1e-12, (k, fv, fu, i, j, got[i, j], ref)
+                checked += 1
+    assert checked == 30
+    assert abs(tab.sub_kernel(31, 0, 0)[32, 32]) > 1e-3          # a w-kernel, not a trivial one
 
 
 def test_w0_kernel_is_pswf():
