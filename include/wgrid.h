@@ -123,6 +123,14 @@ const char* wg_last_error(void);
  * Library FFT kernels (cuFFT) are not counted. */
 uint64_t wg_launch_count(void);
 
+/* Allocation-failure fake for host-side failure tests (the thesis has no counterpart).
+ * after >= 0 arms it: the device allocations of grid_create and worklist_create succeed
+ * `after` more times, then the next one and every later one fail as an out-of-memory
+ * cudaMalloc would, without calling the CUDA runtime, so the failing call returns WG_E_OOM
+ * after freeing what it had allocated.  after < 0 disarms it (the default).  Process-wide;
+ * meant for tests, not for use alongside other work.  Always returns WG_OK. */
+int wg_debug_fail_allocations(int64_t after);
+
 /* ---- grid (output O-1 and O-2 of Sec. 4.3.2) --------------------------------------- */
 typedef struct wg_grid wg_grid;
 

@@ -41,11 +41,35 @@ using namespace wg;
 
 static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Device allocations of grid_create and worklist_create go through this gate.  With the
+// allocation-failure fake armed (wg_debug_fail_allocations), the allocation after the next
+// `after` successful ones fails as cudaMalloc would, without calling the runtime; disarmed
+// (the default, -1) it is cudaMalloc.
+static std::atomic<long long> g_fail_allocs_after{-1};
+
+static cudaError_t dev_malloc(void** p, size_t bytes)
+{
+    long long n = g_fail_allocs_after.load();
+    while (n > 0 && !g_fail_allocs_after.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 extern "C" {
 
 const char* wg_last_error(void) { return t_err; }
 
 uint64_t wg_launch_count(void) { return g_launches.load(); }
+
+int wg_debug_fail_allocations(int64_t after)
+{
+    g_fail_allocs_after.store(after < 0 ? -1 : (long long)after);
+    return WG_OK;
+}
 
 // ---- grid -----------------------------------------------------------------------------
 int grid_create(const wg_grid_desc* d, wg_grid** out)
@@ -70,7 +94,7 @@ int grid_create(const wg_grid_desc* d, wg_grid** out)
     if (d->data) {
         g.data = static_cast<float2*>(d->data);
     } else {
-        if (cudaMalloc(&g.data, bytes) != cudaSuccess) {
+        if (dev_malloc((void**)&g.data, bytes) != cudaSuccess) {
             cudaGetLastError();
             delete h;
             return fail(WG_E_OOM, "cannot allocate a %zu-byte grid", bytes);
@@ -78,9 +102,9 @@ int grid_create(const wg_grid_desc* d, wg_grid** out)
         g.owns = true;
     }
     g.comp = (d->flags & WG_GRID_COMPENSATED) != 0;
-    if (cudaMalloc(&g.norm, sizeof(double) * g.n_chan * g.n_pol) != cudaSuccess ||
-        cudaMalloc(&g.counters, sizeof(unsigned long long) * ST_N) != cudaSuccess ||
-        (g.comp && cudaMalloc(&g.err, bytes) != cudaSuccess)) {
+    if (dev_malloc((void**)&g.norm, sizeof(double) * g.n_chan * g.n_pol) != cudaSuccess ||
+        dev_malloc((void**)&g.counters, sizeof(unsigned long long) * ST_N) != cudaSuccess ||
+        (g.comp && dev_malloc((void**)&g.err, bytes) != cudaSuccess)) {
         cudaGetLastError();
         grid_destroy(h);
         return fail(WG_E_OOM, "cannot allocate normaliser");
@@ -274,7 +298,7 @@ int worklist_create(int64_t max_records, int32_t C, int32_t P, wg_worklist** out
     w.seg_cap = max_records / kSegLenMin + 2;
     bool ok = true;
     auto al = [&](void** p, size_t bytes) {
-        if (ok && cudaMalloc(p, bytes) != cudaSuccess) {
+        if (ok && dev_malloc(p, bytes) != cudaSuccess) {
             cudaGetLastError();
             ok = false;
         }

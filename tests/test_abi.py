@@ -92,3 +92,20 @@ def test_ceiling_rejects_bad_arguments():
     assert wg.lib.ceiling_measure(C["WG_CEIL_SHARED"] + 1, ctypes.byref(v)) == C["WG_E_INVALID_ARG"]
     assert v.value == 0.0
     assert wg.lib.ceiling_measure(C["WG_CEIL_FP32_FMA2"], None) == C["WG_E_INVALID_ARG"]
+
+
+def test_injected_allocation_failure_returns_oom():
+    # the allocation-failure fake fails the next device allocation before the runtime is called,
+    # so grid_create and worklist_create report WG_E_OOM and leave no handle (runs without a GPU)
+    assert wg.lib.wg_debug_fail_allocations(ctypes.c_int64(0)) == C["WG_OK"]
+    try:
+        d = _lib.GridDesc(64, 1, 1, 0, 1.0, None)
+        h = ctypes.c_void_p()
+        assert wg.lib.grid_create(ctypes.byref(d), ctypes.byref(h)) == C["WG_E_OOM"]
+        assert "allocate" in _err() and not h.value
+        w = ctypes.c_void_p()
+        rc = wg.lib.worklist_create(ctypes.c_int64(1000), ctypes.c_int32(2), ctypes.c_int32(4), ctypes.byref(w))
+        assert rc == C["WG_E_OOM"]
+        assert "work list" in _err() and not w.value
+    finally:
+        assert wg.lib.wg_debug_fail_allocations(ctypes.c_int64(-1)) == C["WG_OK"]
