@@ -120,7 +120,7 @@ extern "C" {
 const char* wg_last_error(void);
 
 /* Number of CUDA kernels this library has launched in this process so far (all devices).
- * Library FFT kernels (cuFFT) are not counted. */
+ * Library FFT kernels (cuFFT) are not counted.  A measurement aid; not in the thesis. */
 uint64_t wg_launch_count(void);
 
 /* Allocation-failure fake for host-side failure tests (the thesis has no counterpart).
@@ -147,11 +147,15 @@ typedef struct wg_grid_desc {
 /* Creates a grid and its FP64 normaliser accumulators N_p [n_chan][n_pol] (eq.
  * "normalizer"), both zeroed.  Synchronises the device.  Errors: INVALID_ARG, OOM, CUDA. */
 int grid_create(const wg_grid_desc* desc, wg_grid** out);
+/* Frees the grid's library-owned device memory (O-1 and O-2 of Sec. 4.3.2; never a caller's
+ * external buffer) and the handle.  NULL is accepted.  Synchronises the device (cudaFree).  Returns WG_OK. */
 int grid_destroy(wg_grid* grid);
-/* Zeroes the grid, the normaliser and the statistics counters on `stream`. */
+/* Zeroes the grid O-1, the normaliser O-2 (Sec. 4.3.2) and the statistics counters on
+ * `stream`.  Errors: INVALID_ARG, CUDA. */
 int grid_zero(wg_grid* grid, void* stream);
-/* Device pointers of the grid data (complex64, layout above) and of N_p (double
- * [n_chan][n_pol]).  Either output may be NULL. */
+/* Device pointers of the grid data O-1 (complex64, layout above) and of N_p, O-2 (double
+ * [n_chan][n_pol]; Sec. 4.3.2), owned by the grid.  Either output may be NULL.
+ * Errors: INVALID_ARG. */
 int grid_device_ptrs(const wg_grid* grid, void** data, double** normaliser);
 
 /* ---- convolution functions (inputs C-1, C-2, C-3 of Sec. 4.2.2) -------------------- */
@@ -181,16 +185,19 @@ typedef struct wg_table_desc {
  *         OOB_SUPPORT (support > 1023), OOM, CUDA. */
 int conv_table_build(const wg_table_desc* desc, wg_table** out, void* stream);
 
-/* Builds a table from caller-provided host data in the same layout as C-1/C-2/C-3:
+/* Builds a table from caller-provided host data in the same layout as C-1/C-2/C-3 (Sec.
+ * 4.2.2), for kernels made elsewhere:
  * data = complex double [sum_k beta^2 S_k^2] (interleaved re, im), supports [K] (odd),
  * zeta [K beta^2].  Stored as complex float32.  Synchronises the device. */
 int conv_table_import(int32_t n_wplanes, int32_t oversample, double w_max, double du,
                       int32_t taper_support, const int32_t* supports, const double* data,
                       const double* zeta, wg_table** out);
+/* Frees the table's device memory (C-1 .. C-3 of Sec. 4.2.2 and their reduced-precision copy)
+ * and the handle.  NULL is accepted.  Synchronises the device (cudaFree).  Returns WG_OK. */
 int table_destroy(wg_table* table);
 
 /* Sets the storage the gridder reads (WG_F32, WG_BF16, WG_F16), converting the float32 samples
- * with round-to-nearest-even.  Synchronises the device.  Errors: INVALID_ARG, OOM, CUDA. */
+ * with round-to-nearest-even (a precision variant; the thesis stores float32).  Synchronises the device.  Errors: INVALID_ARG, OOM, CUDA. */
 int table_set_store(wg_table* table, int32_t store_dtype);
 
 typedef struct wg_table_info {
@@ -205,9 +212,12 @@ typedef struct wg_table_info {
     int32_t reserved;
     const void* data_lp;      /* device complex bf16/f16 [n_samples], or NULL for WG_F32 */
 } wg_table_info;
+/* Sizes and device pointers (owned by the table) of C-1 .. C-3 (Sec. 4.2.2).
+ * Errors: INVALID_ARG. */
 int table_info(const wg_table* table, wg_table_info* info);
-/* Copies C-1 (complex float32, interleaved), C-3 and C-2 to host buffers sized from
- * table_info; any pointer may be NULL.  Synchronises the device. */
+/* Copies C-1 (complex float32, interleaved), C-3 and C-2 (Sec. 4.2.2) to caller-owned host
+ * buffers sized from table_info; any pointer may be NULL.  Synchronises the device.
+ * Errors: INVALID_ARG, CUDA. */
 int table_copy_to_host(const wg_table* table, float* data, double* zeta, int32_t* supports,
                        int32_t* offsets);
 
@@ -234,6 +244,8 @@ typedef struct wg_worklist wg_worklist;
  * 41 + 16 n_pol bytes per record (placement, entries, weighted visibilities, runs and the
  * degridder's per-entry sums).  Errors: INVALID_ARG, OOM. */
 int worklist_create(int64_t max_records, int32_t n_chan, int32_t n_pol, wg_worklist** out);
+/* Frees the work list's device buffers (the preparation outputs of Sec. 4.3.4) and the handle.  NULL is accepted.  Synchronises the
+ * device (cudaFree).  Returns WG_OK. */
 int worklist_destroy(wg_worklist* wl);
 
 typedef struct wg_stats {
@@ -280,7 +292,8 @@ int vis_compress(const wg_grid* grid, const wg_table* table, const wg_vis_in* in
 /* Copies the work list's statistics (Sec. 4.3.4) to *out.  Synchronises `stream`. */
 int worklist_stats(const wg_worklist* wl, wg_stats* out, void* stream);
 
-/* Device views of the work list, for inspection and tests.  entries: int32 [n][4] with
+/* Device views (owned by the work list) of the gridded-record list of Algorithms "index" and
+ * "compressindex" (Sec. 4.3.3), for inspection and tests.  entries: int32 [n][4] with
  * {x0 | y0 << 16, (-x0 mod S) | (-y0 mod S) << 16, z, k | chan << 16}; gamma: complex64
  * [n][n_pol]; runs: int32 [n][2] first and last row of each gridded run (first and last
  * record when interleaved); rec_class: uint8
@@ -325,10 +338,11 @@ typedef struct wg_plan {
  * Errors: INVALID_ARG, CUDA. */
 int worklist_plan(wg_worklist* wl, const wg_table* table, const wg_plan* plan, void* stream);
 
-/* The work list's current plan. */
+/* The work list's current plan (not in the thesis).  Errors: INVALID_ARG. */
 int worklist_get_plan(const wg_worklist* wl, wg_plan* plan);
 
-/* Times grid_vis on the batch prepared on `wl` under each of the n_candidates plans (NULL or
+/* Autotuner (not in the thesis; it picks the GPU work decomposition of the gridding phase,
+ * Sec. 4.3.3).  Times grid_vis on the batch prepared on `wl` under each of the n_candidates plans (NULL or
  * 0: seg_len {64, 128, 256} x slots {128, 256} x flags {0, WG_PLAN_FIXED_R}), `repeats`
  * timed launches each after one warm-up launch (CUDA events on `stream`), keeps the fastest
  * plan in `wl` and copies it to *best (may be NULL), writes its mean milliseconds per launch

@@ -109,3 +109,17 @@ def test_injected_allocation_failure_returns_oom():
         assert "work list" in _err() and not w.value
     finally:
         assert wg.lib.wg_debug_fail_allocations(ctypes.c_int64(-1)) == C["WG_OK"]
+
+
+def test_every_declaration_cites_its_passage():
+    # each function's comment block names the thesis passage it follows, or says that the
+    # thesis has no counterpart
+    import re
+    txt = open(_lib.HEADER).read()
+    decls = [(m.start(), m.group(1)) for m in
+             re.finditer(r"^\s*(?:int|const char\*|uint64_t)\s+(\w+)\s*\(", txt, flags=re.M)]
+    prev = 0
+    for pos, name in decls:
+        comments = " ".join(re.findall(r"/\*.*?\*/", txt[prev:pos], flags=re.S))
+        assert re.search(r"Sec\.|Algorithm|eq\.|thesis|no counterpart", comments), name
+        prev = pos
