@@ -408,15 +408,23 @@ int grid_correct(wg_grid* grid, const wg_table* table, int32_t mode, float* imag
  *     serialise them.
  *   - The caller passes the output grid and normaliser as device pointers (layouts as for
  *     grid_create); both are accumulated into.  `table` comes from conv_table_build or
- *     conv_table_import.  Nothing is allocated or freed: no cudaMalloc, no cudaFree. */
+ *     conv_table_import.  Nothing is allocated or freed: no cudaMalloc, no cudaFree.
+ *   - Visibilities are complex64 (8-byte aligned) or complex half with scales (4-byte
+ *     aligned), as for vis_compress; `compress` is 0 or WG_PREP_COMPRESS.
+ * Errors: INVALID_ARG, SHAPE, OOB_SUPPORT, CAPACITY, CUDA. */
 #define WG_NOALLOC_MAX_RECORDS 65536
 #define WG_NOALLOC_MAX_CHAN 64
 
 typedef struct wg_grid_view {
     int32_t n, n_pol, n_chan, reserved; /* as wg_grid_desc                                */
-    double du;                          /* cell size in wavelengths                      */
+    double du;                          /* cell size in wavelengths, positive and finite */
     void* data;                         /* device complex64 [n_chan][N][N][n_pol], 16-B aligned */
     double* normaliser;                 /* device double [n_chan][n_pol]                  */
+    int64_t* dropped;                   /* optional (NULL: not reported) device int64,    */
+                                        /* 8-B aligned: overwritten, stream-ordered, with */
+                                        /* the call's count of entries rejected by the    */
+                                        /* device-side bounds checks (wg_stats.dropped:   */
+                                        /* always 0 unless an internal error occurred)    */
 } wg_grid_view;
 
 int grid_vis_noalloc(const wg_grid_view* grid, const wg_table* table, const wg_vis_in* in,

@@ -21,6 +21,8 @@ int fail(int code, const char* fmt, ...)
     return code;
 }
 
+void clear_error() { t_err[0] = 0; }
+
 int cuda_fail(cudaError_t e, const char* what)
 {
     cudaGetLastError();

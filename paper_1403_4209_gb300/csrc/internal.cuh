@@ -16,6 +16,7 @@ namespace wg {
 // ---- errors -------------------------------------------------------------------------
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
+void clear_error();   // empties this thread's wg_last_error() message
 #define WG_CUDA(call)                                   \
     do {                                                \
         cudaError_t e_ = (call);                        \

@@ -71,21 +71,31 @@ using namespace wg;
 extern "C" int grid_vis_noalloc(const wg_grid_view* view, const wg_table* th, const wg_vis_in* in, int32_t compress,
                                 void* stream)
 {
+    clear_error();
     if (!view || !th || !in) return fail(WG_E_INVALID_ARG, "grid_vis_noalloc: null argument");
     const Table& t = th->t;
     if (view->n < 8 || view->n > 32768 || (view->n & 1)) return fail(WG_E_INVALID_ARG, "grid side N=%d must be even in [8, 32768]", view->n);
+    if (!(view->du > 0.0) || !std::isfinite(view->du))
+        return fail(WG_E_INVALID_ARG, "cell size du must be positive and finite");
     if (view->n_pol != 1 && view->n_pol != 2 && view->n_pol != 4) return fail(WG_E_INVALID_ARG, "n_pol must be 1, 2 or 4");
     if (view->n_chan < 1 || view->n_chan > WG_NOALLOC_MAX_CHAN)
         return fail(WG_E_CAPACITY, "n_chan=%d exceeds the no-allocation limit %d", view->n_chan, WG_NOALLOC_MAX_CHAN);
     if (!view->data || !view->normaliser) return fail(WG_E_INVALID_ARG, "grid_vis_noalloc: null grid or normaliser");
     if (reinterpret_cast<uintptr_t>(view->data) & 15) return fail(WG_E_INVALID_ARG, "grid buffer must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(view->dropped) & 7) return fail(WG_E_INVALID_ARG, "dropped must be 8-byte aligned");
     if (in->n_chan != view->n_chan || in->n_pol != view->n_pol) return fail(WG_E_SHAPE, "vis shape differs from the grid's");
     if (in->n_rows < 0) return fail(WG_E_INVALID_ARG, "n_rows must be >= 0");
     if (compress != 0 && compress != WG_PREP_COMPRESS)
         return fail(WG_E_INVALID_ARG, "compress must be 0 or WG_PREP_COMPRESS (got %d)", compress);
     if (in->n_rows > 0 && (!in->uvw || !in->freq_hz || !in->vis || !in->weight || !in->flag))
         return fail(WG_E_INVALID_ARG, "null input array");
-    if (reinterpret_cast<uintptr_t>(in->vis) & 7) return fail(WG_E_INVALID_ARG, "vis must be 8-byte aligned");
+    if (in->vis_dtype != WG_VIS_COMPLEX64 && in->vis_dtype != WG_VIS_COMPLEX_HALF)
+        return fail(WG_E_INVALID_ARG, "unknown vis_dtype %d", in->vis_dtype);
+    if (in->vis_dtype == WG_VIS_COMPLEX_HALF && in->n_rows > 0 && !in->vis_scale)
+        return fail(WG_E_INVALID_ARG, "vis_scale is required for half-precision visibilities");
+    // the element size: 8 bytes for complex64, 4 for complex half (as vis_compress checks)
+    if (reinterpret_cast<uintptr_t>(in->vis) & (in->vis_dtype == WG_VIS_COMPLEX64 ? 7 : 3))
+        return fail(WG_E_INVALID_ARG, "vis is not aligned to its element size");
     if (std::fabs(t.du - view->du) > 1e-12 * view->du) return fail(WG_E_SHAPE, "table du differs from grid du");
     if (t.max_support > view->n) return fail(WG_E_OOB_SUPPORT, "support %d larger than the grid (%d)", t.max_support, view->n);
     const int64_t records = in->n_rows * (int64_t)in->n_chan;
@@ -136,7 +146,16 @@ extern "C" int grid_vis_noalloc(const wg_grid_view* view, const wg_table* th, co
     g.norm = view->normaliser;
     g.counters = counters;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the statistics slot is written by every call but read by none: start it at zero so it
+    // holds this call's counts rather than a sum over earlier callers
+    WG_CUDA(cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * ST_N, s));
     rc = launch_prep(t, g, *in, compress, w, s);
     if (rc != WG_OK) return rc;
-    return launch_grid(g, t, w, s);
+    rc = launch_grid(g, t, w, s);
+    if (rc != WG_OK) return rc;
+    // entries rejected by the device-side bounds checks of preparation and gridding (cleared by
+    // launch_prep), copied out for the caller
+    if (view->dropped)
+        WG_CUDA(cudaMemcpyAsync(view->dropped, w.scal + 3, sizeof(long long), cudaMemcpyDeviceToDevice, s));
+    return WG_OK;
 }
