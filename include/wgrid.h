@@ -265,8 +265,10 @@ typedef struct wg_stats {
  *      lam_inv = f_c / 299792458;  sc = lam_inv * (beta / du)
  *      tu = u' sc, tv = v' sc, w = w' lam_inv;  if w' < 0: negate all three, psi = -1
  *      q = ceil(t - 0.5);  x_c = ceil((q - beta/2) / beta) (integer);  frac = q - beta x_c
- *      x = N/2 + x_c;  k = floor((K-1) sqrt(w / w_max) + 0.5)  (k = 0 if K = 1), evaluated
- *      without a square root as the number of plane bounds w_max ((m - 1/2)/(K-1))^2 <= w
+ *      x = N/2 + x_c;  k = the nearest plane in sqrt(w) (Sec. 2.2.1), decided without a
+ *      square root: k = the number of m in 1..K-1 with w >= b_m, where b_m = w_max t_m^2 and
+ *      t_m = (m - 1/2)/(K-1) (each product rounded once), so ties go to the upper plane and
+ *      w >= b_K is beyond the last plane (k = 0 if K = 1)
  *      footprint origin (x - (S_k-1)/2, y - (S_k-1)/2); kernel pointer
  *      z = offset_k + ((frac_v - lo) beta + (frac_u - lo)) S_k^2, lo = -((beta-1)/2)
  *      griddable: k <= K-1, footprint inside the grid, some polarisation unflagged;
