@@ -62,7 +62,7 @@ def test_interleaved_grid_and_normaliser(case):
     wl, (g, t, b, w), ref = case
     got = g.data.cpu().numpy()
     assert got.shape[0] == 1
-    assert rel_l2(got, ref["grid"]) < 1e-5 and max_rel(got, ref["grid"]) < 1e-4
+    assert rel_l2(got, ref["grid"]) < 1e-5 and max_rel(got, ref["grid"]) < 1e-5
     assert max_rel(g.normaliser().cpu().numpy(), ref["norm"]) < 1e-5
 
 
