@@ -77,22 +77,29 @@ def exact_screen(w: float, l: np.ndarray, m: np.ndarray) -> np.ndarray:
     return np.where(inside, np.exp(2j * np.pi * w * nm1), 0.0)
 
 
-def _oversampled_plane(w, n_k, beta, du, taper_1d, screen):
-    """Steps 1-2: the (beta*N_k)^2 oversampled C_w, centred (offset 0 at index M/2)."""
-    M = beta * n_k
+def _patch(w, n_k, du, taper_1d, screen):
+    """Step 1: the N_k x N_k image-plane patch taper(l) taper(m) gbar_w(l, m), and its taper row."""
     idx = np.arange(n_k)
     eta = 2.0 * (idx - n_k // 2) / n_k
     l = eta / (2.0 * du)
     t = taper_1d(l, eta)
     t = np.where(idx == 0, 0.0, t)                       # eta = -1 sample has no partner
     L, Mm = np.meshgrid(l, l, indexing="xy")             # [m][l]
-    patch = (t[:, None] * t[None, :]) * screen(w, L, Mm)
+    return (t[:, None] * t[None, :]) * screen(w, L, Mm)
+
+
+def _oversampled_plane(w, n_k, beta, du, taper_1d, screen):
+    """Step 2: the (beta*N_k)^2 oversampled C_w, centred (offset 0 at index M/2)."""
+    M = beta * n_k
     padded = np.zeros((M, M), dtype=np.complex128)
     o = M // 2 - n_k // 2
-    padded[o:o + n_k, o:o + n_k] = patch
-    C = np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(padded)))
-    norm = float(np.real(np.sum((t[:, None] * t[None, :]) * screen(0.0, L, Mm))))  # C_0(0,0)
-    return C, norm
+    padded[o:o + n_k, o:o + n_k] = _patch(w, n_k, du, taper_1d, screen)
+    return np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(padded)))
+
+
+def _dc_norm(n_k, du, taper_1d, screen):
+    """Step 3's constant: C_0(0,0), the DC value of the w = 0 patch's transform (its sum)."""
+    return float(np.real(np.sum(_patch(0.0, n_k, du, taper_1d, screen))))
 
 
 def threshold_support(C: np.ndarray, beta: int, threshold: float) -> int:
@@ -125,24 +132,36 @@ def _trim(C: np.ndarray, beta: int, S: int) -> np.ndarray:
 def build_table(du: float, n_wplanes: int, w_max: float, beta: int, taper_support: int = 7,
                 supports: Optional[Sequence[int]] = None, n_k: Optional[int] = None,
                 threshold: float = 1e-3, taper: Optional[Callable] = None,
-                screen: Optional[Callable] = None) -> Table:
+                screen: Optional[Callable] = None, planes: Optional[Sequence[int]] = None) -> Table:
     """Algorithm "convgen".  `taper(l, eta)` and `screen(w, l, m)` may be replaced (the
-    pins substitute a Gaussian taper and the paraxial screen to reach a closed form)."""
+    pins substitute a Gaussian taper and the paraxial screen to reach a closed form).
+
+    `planes` (prescribed supports only) builds the kernels of those planes alone: every plane
+    is computed independently of the others (the normalisation constant comes from the w = 0
+    patch), so the built planes are identical to a full build; the others keep their layout
+    (supports, offsets) with zero samples, zero zeta and threshold support 0.  It bounds the
+    host time and memory of large tables (64 planes of 4096^2 transforms) when a test's
+    records touch only some planes."""
     K = n_wplanes
     c = bandwidth(taper_support)
     if taper is None:
         taper = lambda l, eta: psi0(c, eta)  # noqa: E731
     if screen is None:
         screen = exact_screen
+    if planes is not None and supports is None:
+        raise ValueError("a plane subset needs prescribed supports")
+    todo = set(range(K)) if planes is None else {int(k) for k in planes}
+    if any(k < 0 or k >= K for k in todo):
+        raise ValueError("plane index out of range")
     w_planes = w_plane_values(K, w_max)
     if n_k is None:
         n_k = default_nk(max(supports) if supports is not None else 4 * taper_support)
-    planes, norm = [], None
-    for k in range(K):
-        C, norm = _oversampled_plane(w_planes[k], n_k, beta, du, taper, screen)
-        planes.append(C)
-    planes = [C / norm for C in planes]
-    thr = np.array([threshold_support(C, beta, threshold) for C in planes], dtype=np.int32)
+    norm = _dc_norm(n_k, du, taper, screen)
+    built, thr = {}, np.zeros(K, dtype=np.int32)
+    for k in sorted(todo):
+        C = _oversampled_plane(w_planes[k], n_k, beta, du, taper, screen) / norm
+        thr[k] = threshold_support(C, beta, threshold)
+        built[k] = C if supports is None else _trim(C, beta, int(supports[k]))
     sup = np.asarray(supports, dtype=np.int32) if supports is not None else thr.copy()
     if np.any(sup % 2 == 0) or np.any(sup < 1):
         raise ValueError("supports must be odd and positive")
@@ -150,7 +169,10 @@ def build_table(du: float, n_wplanes: int, w_max: float, beta: int, taper_suppor
     off = 0
     for k in range(K):
         S = int(sup[k])
-        sub = _trim(planes[k], beta, S)                  # [beta, beta, S, S]
+        if k in built:
+            sub = built[k] if supports is not None else _trim(built[k], beta, S)   # [beta, beta, S, S]
+        else:
+            sub = np.zeros((beta, beta, S, S), dtype=np.complex128)
         offsets.append(off)
         data.append(sub.reshape(-1))
         zeta.append(sub.real.sum(axis=(2, 3)).reshape(-1))
