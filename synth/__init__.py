@@ -216,29 +216,11 @@ def _flags(rows, C, P, frac, seed, device):
     return torch.maximum(f, allf.expand(rows, C, P)).contiguous()
 
 
-def make(name: str, device: str = "cpu", flag_frac: float = 0.0, n_times: Optional[int] = None,
-         n_chan: Optional[int] = None, n_baselines: Optional[int] = None,
-         chan_group: Optional[int] = None, chan0: int = 0) -> Workload:
-    """Build one of the named workloads.
+_SEEDS = {"w0_small": 1000, "wproj_2k": 1001, "degrid_1k": 1002, "batch_8k": 1004, "mfs_2k": 1005}
 
-    name: "w0_small"   : plain w=0 gridding, 32 stations in a 2 km disk, 496 baselines x 256
-                         steps at 10 s, dec +45, 150 MHz, 1 pol, N=512, S=7, beta=8, K=1.
-          "wproj_2k"   : 64 stations in a 3 km Gaussian layout, 2016 baselines x 3600 steps at
-                         1 s, 16 channels 120-180 MHz, 4 pols, N=2048, K=32 sqrt(w)-spaced
-                         planes with supports 9..65, beta=8.
-          "degrid_1k"  : 64 stations, 600 steps, 4 channels 120-180 MHz, 4 pols, N=1024, K=16.
-          "batch_8k"   : 256 stations log-radial to 10 km, 1800 steps, 64 channels
-                         50-350 MHz, 1 pol, N=8192, K=64, supports 9..129.
-          "mfs_2k"     : the wproj_2k geometry with 16 narrow channels (12.2 kHz apart from
-                         150 MHz, a LOFAR subband split 16 ways), for channel interleaving.
-    n_times / n_chan / n_baselines shrink a workload to a seeded slice of the same geometry;
-    chan0 is the first channel of an n_chan slice.
-    chan_group: vis, weight and flag become lists of [rows, chan_group, P] tensors, one per
-    group of consecutive channels, each drawn with its own seed (seed + 7919 * group index);
-    the (all-ones) weight tensor is shared by the groups."""
-    seeds = {"w0_small": 1000, "wproj_2k": 1001, "degrid_1k": 1002, "batch_8k": 1004, "mfs_2k": 1005}
-    seed = seeds[name]
-    rng = np.random.default_rng(seed)
+
+def _spec(name: str, rng: np.random.Generator):
+    """Station layout (the first draws from rng) and the fixed parameters of a named workload."""
     if name == "w0_small":
         enu = stations_uniform_disk(32, 2000.0, rng)
         T, dt, dec = 256, 10.0, 45.0
@@ -271,19 +253,84 @@ def make(name: str, device: str = "cpu", flag_frac: float = 0.0, n_times: Option
         noise = 0.01
     else:
         raise KeyError(name)
+    return enu, T, dt, dec, freq, P, N, K, beta, S_lo, S_hi, taper, noise
+
+
+def full_tracks(name: str):
+    """The full workload's uvw tracks [baselines, times, 3] in metres and its channel
+    frequencies [C] in Hz (the same seeded layout as make(name)); for choosing slices."""
+    rng = np.random.default_rng(_SEEDS[name])
+    enu, T, dt, dec, freq, *_ = _spec(name, rng)
+    uvw = uvw_tracks(enu, T, dt, dec, baselines=baseline_pairs(enu.shape[0]))
+    return uvw.reshape(-1, T, 3), np.asarray(freq, dtype=np.float64)
+
+
+def outer_w_slice(name: str, n_times: int, n_top: int, n_spread: int, stride: int = 97):
+    """A slice that reaches the workload's outermost w-planes: the n_times steps around the
+    largest |w| of the track, the n_top baselines with the largest |w| in those steps, and
+    n_spread further baselines taken every `stride` along the baseline list.  Returns
+    (sorted baseline indices, first time step) for make(baselines=..., t_start=...)."""
+    tracks, _ = full_tracks(name)
+    B, T, _ = tracks.shape
+    aw = np.abs(tracks[:, :, 2])
+    t_star = int(np.argmax(aw.max(axis=0)))
+    t0 = min(max(0, t_star - n_times // 2), T - n_times)
+    w_win = aw[:, t0:t0 + n_times].max(axis=1)
+    top = np.argsort(w_win)[::-1][:n_top]
+    rest = np.setdiff1d(np.arange(0, B, stride), top)[:n_spread]
+    return np.sort(np.concatenate([top, rest])), t0
+
+
+def make(name: str, device: str = "cpu", flag_frac: float = 0.0, n_times: Optional[int] = None,
+         n_chan: Optional[int] = None, n_baselines: Optional[int] = None,
+         chan_group: Optional[int] = None, chan0: int = 0, baselines=None,
+         t_start: Optional[int] = None) -> Workload:
+    """Build one of the named workloads.
+
+    name: "w0_small"   : plain w=0 gridding, 32 stations in a 2 km disk, 496 baselines x 256
+                         steps at 10 s, dec +45, 150 MHz, 1 pol, N=512, S=7, beta=8, K=1.
+          "wproj_2k"   : 64 stations in a 3 km Gaussian layout, 2016 baselines x 3600 steps at
+                         1 s, 16 channels 120-180 MHz, 4 pols, N=2048, K=32 sqrt(w)-spaced
+                         planes with supports 9..65, beta=8.
+          "degrid_1k"  : 64 stations, 600 steps, 4 channels 120-180 MHz, 4 pols, N=1024, K=16.
+          "batch_8k"   : 256 stations log-radial to 10 km, 1800 steps, 64 channels
+                         50-350 MHz, 1 pol, N=8192, K=64, supports 9..129.
+          "mfs_2k"     : the wproj_2k geometry with 16 narrow channels (12.2 kHz apart from
+                         150 MHz, a LOFAR subband split 16 ways), for channel interleaving.
+    n_times / n_chan / n_baselines shrink a workload to a seeded slice of the same geometry;
+    chan0 is the first channel of an n_chan slice.  `baselines` (indices into the workload's
+    baseline list, in the order given) replaces the first n_baselines; `t_start` is the first
+    time step of an n_times slice (default: the block centred on transit).
+    chan_group: vis, weight and flag become lists of [rows, chan_group, P] tensors, one per
+    group of consecutive channels, each drawn with its own seed (seed + 7919 * group index);
+    the (all-ones) weight tensor is shared by the groups."""
+    seed = _SEEDS[name]
+    rng = np.random.default_rng(seed)
+    enu, T, dt, dec, freq, P, N, K, beta, S_lo, S_hi, taper, noise = _spec(name, rng)
     sky = point_sources(5, rng)
     pairs = baseline_pairs(enu.shape[0])
     supports = support_schedule(S_lo, S_hi, K)
     # geometry of the FULL workload fixes cell size and w_max, so slices share it
     uvw_full = uvw_tracks(enu, T, dt, dec, baselines=pairs)
     du, w_max = cell_and_wmax(uvw_full, freq, N, max(supports))
-    if n_baselines is not None:
+    b_idx = np.arange(len(pairs))
+    if baselines is not None:
+        b_idx = np.asarray(baselines, dtype=np.int64).reshape(-1)
+        if b_idx.size and (b_idx.min() < 0 or b_idx.max() >= len(pairs)):
+            raise ValueError("baseline index out of range")
+        pairs = pairs[b_idx]
+    elif n_baselines is not None:
         pairs = pairs[:n_baselines]
+        b_idx = b_idx[:n_baselines]
     T_used = T if n_times is None else n_times
-    if n_times is not None or n_baselines is not None:
-        # a contiguous block of time steps around transit for the chosen baselines
-        t_idx = np.arange(T)[(T - T_used) // 2:(T - T_used) // 2 + T_used]
-        uvw = uvw_full.reshape(-1, T, 3)[:len(pairs)][:, t_idx]
+    if n_times is not None or n_baselines is not None or baselines is not None:
+        # a contiguous block of time steps (centred on transit unless t_start is given) for the
+        # chosen baselines
+        t0 = (T - T_used) // 2 if t_start is None else int(t_start)
+        if t0 < 0 or t0 + T_used > T:
+            raise ValueError("time slice [%d, %d) outside the %d steps" % (t0, t0 + T_used, T))
+        t_idx = np.arange(t0, t0 + T_used)
+        uvw = uvw_full.reshape(-1, T, 3)[b_idx][:, t_idx]
         uvw = np.ascontiguousarray(uvw.reshape(-1, 3))
     else:
         uvw = uvw_full
