@@ -7,10 +7,10 @@ grid_correct (inverse FFT, normalisation, taper and sinc correction, Stokes I). 
 build is one-off and outside the timed region, as in the thesis (Sec. 5.3.1 times the
 gridder only).  Inputs (6.2 GB for the default workload) are larger than L2.
 
-value  = total grid-point updates per second of the whole step, summed over ranks: every
-         griddable record x S^2 x polarisations, compressed records included as if gridded
-         (the thesis's "total rate", Sec. 5.3.1); the "real" rate counts only the updates the
-         gridder performed.
+value  = real grid-point updates per second of the whole step, summed over ranks: the updates
+         the gridder performs, gridded records x S^2 x polarisations (the thesis's "real rate",
+         Sec. 5.3.1).  The "total" rate, which also counts the compressed records as if they
+         were gridded, is reported beside it under `rates`.
 e2e    = the same metric with pinned host inputs copied to the device and the Stokes-I image
          copied back inside the timed region of every step (double-buffered: the copies of the
          next step overlap the current step's compute).
@@ -57,8 +57,14 @@ WORKLOADS = {
                 "FP32 table; compression on; 8 groups of 8 channels through one reused work list, the whole "
                 "step captured in one CUDA graph, gridder plan autotuned per group",
 }
+# the unit of `value` and `e2e` in both arms (the driver divides one arm's value by the other's)
+UNIT = "G grid-point updates/s (real rate: updates the gridder performs, whole step)"
+# precision variants timed beside the plain FP32 path: (name, table store, half vis, compensated)
+VARIANTS = (("fp32+compensated", "f32", False, True), ("f16 table", "f16", False, False),
+            ("bf16 table", "bf16", False, False), ("f16 vis", "f32", True, False),
+            ("f16 table+f16 vis+compensated", "f16", True, True))
 # bounded CPU samples of the same geometry (channels, time steps)
-CPU_SAMPLE = {"wproj_2k": (16, 1200), "w0_small": (1, 256), "batch_8k": (2, 40), "degrid_1k": (1, 300),
+CPU_SAMPLE = {"wproj_2k": (16, 1200), "w0_small": (1, 256), "batch_8k": (2, 720), "degrid_1k": (1, 300),
               "mfs_2k": (4, 1200), "wstack_2k": (2, 1200)}
 # worker processes of the CPU baseline (one channel each) where the oracle's table build is cheap
 CPU_PROCS = {"wproj_2k": 16}
@@ -308,7 +314,7 @@ def run_ours(args, rank, world, local_rank):
     barrier(world)
     real = st["updates"]
     total = st["updates"] + st["updates_saved"]
-    value = whole_job_rate(total, ms, world)
+    value = whole_job_rate(real, ms, world)
 
     # end to end: every step copies its inputs from pinned host memory and reads its Stokes-I
     # image back.  The copies of step k+1 run on a copy stream into the other of two device
@@ -401,8 +407,8 @@ def run_ours(args, rank, world, local_rank):
     c1.record(cstream)
     torch.cuda.synchronize()
     ms_h2d = c0.elapsed_time(c1) / 3
-    e2e = {"value": round(whole_job_rate(total, ms_e2e, world), 3), "unit": "G grid-point updates/s",
-           "ms_per_step": round(ms_e2e, 3), "steps": ne, "h2d_bytes_per_step": int(h2d),
+    e2e = {"value": round(whole_job_rate(real, ms_e2e, world), 3), "unit": UNIT,
+           "total_rate_G": round(whole_job_rate(total, ms_e2e, world), 3), "ms_per_step": round(ms_e2e, 3), "steps": ne, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h), "h2d_alone_ms": round(ms_h2d, 3),
            "h2d_gbs": round(h2d / (ms_h2d * 1e-3) / 1e9, 1),
            "copy_hidden_frac": None if copy_hidden is None else round(copy_hidden, 3),
@@ -415,9 +421,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_variants and not inter and not stack_k:
         vis_h, scale_h = synth.to_half_vis(wl.vis)
         batch_h = wg.VisBatch(uvw_d, freq_d, vis_h, wl.weight, wl.flag, vis_scale=scale_h)
-        for name, store, half, comp in (("fp32+compensated", "f32", False, True), ("f16 table", "f16", False, False),
-                                        ("bf16 table", "bf16", False, False), ("f16 vis", "f32", True, False),
-                                        ("f16 table+f16 vis+compensated", "f16", True, True)):
+        for name, store, half, comp in VARIANTS:
             tv = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support,
                                     supports=wl.supports, store=store)
             gv = wg.Grid(wl.n_grid, wl.du, wl.n_pol, wl.n_chan, device=dev, compensated=comp)
@@ -439,7 +443,8 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize()
             ms_v = evs[0].elapsed_time(evs[1]) / nv
             variants[name] = {"ms_per_step": round(ms_v, 3), "gridder_ms": round(evs[2].elapsed_time(evs[3]), 3),
-                              "value": round(total / (ms_v * 1e-3) / 1e9, 1)}
+                              "value": round(real / (ms_v * 1e-3) / 1e9, 1),
+                              "total_rate_G": round(total / (ms_v * 1e-3) / 1e9, 1)}
             del tv, gv
         del batch_h, vis_h
 
@@ -497,7 +502,7 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": "gridding/degridding G grid-point updates/s and % roofline at stated grid error",
         "value": round(value, 3),
-        "unit": "G grid-point updates/s (total rate, whole step)",
+        "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -508,11 +513,12 @@ def run_ours(args, rank, world, local_rank):
                    "records_per_step": wl.rows * wl.n_chan, "l2": "inputs larger than L2 (no flush needed)",
                    "plan_seg_len_slots_fixed_r": plan,
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "rates": {"total_step_G": round(value, 3),
-                  "real_step_G": round(world * real / (ms * 1e-3) / 1e9, 3),
+        "rates": {"real_step_G": round(value, 3),
+                  "total_step_G": round(whole_job_rate(total, ms, world), 3),
                   "real_gridder_G": round(real / (t_grid * 1e-3) / 1e9, 3),
                   "total_gridder_G": round(total / (t_grid * 1e-3) / 1e9, 3),
-                  "degrid_G": round(total / (t_degrid * 1e-3) / 1e9, 3),
+                  "degrid_real_G": round(real / (t_degrid * 1e-3) / 1e9, 3),
+                  "degrid_total_G": round(total / (t_degrid * 1e-3) / 1e9, 3),
                   "gridder_ms": round(t_grid, 4), "degrid_ms": round(t_degrid, 4),
                   "records_gridded": st["gridded"], "records_compressed": st["compressed"],
                   "record_rate_real_M": round(st["gridded"] / (t_grid * 1e-3) / 1e6, 1),
@@ -541,8 +547,83 @@ def run_ours(args, rank, world, local_rank):
         nc, nt = CPU_SAMPLE[args.workload]
         procs = min(CPU_PROCS.get(args.workload, 1), os.cpu_count() or 1, nc)
         line["cpu_baseline"] = cpu_sample(args.workload, nc if procs > 1 else min(nc, 4), nt, procs)
-        line["grid_error"] = grid_error_sample(args.workload, dev, plan, inter, stack_k)
+        if args.workload == "wproj_2k" and args.n_chan is None and args.n_times is None:
+            errs = variant_errors(dev, plan)
+            line["grid_error"] = errs.pop("fp32")
+            for name, e in errs.items():
+                if name in variants:
+                    variants[name]["grid_error"] = e
+        else:
+            line["grid_error"] = grid_error_sample(args.workload, dev, plan, inter, stack_k)
     return line
+
+
+def _table_worker(args):
+    """One worker of oracle_table_parallel: the kernels of a few planes, as {plane: (samples, zeta)}."""
+    du, K, w_max, beta, taper, supports, planes = args
+    import oracle
+    t = oracle.build_table(du, K, w_max, beta, taper, supports=supports, planes=planes)
+    b2 = beta * beta
+    return {k: (t.data[t.offsets[k]:t.offsets[k] + b2 * int(t.supports[k]) ** 2].copy(),
+                t.zeta[k * b2:(k + 1) * b2].copy()) for k in planes}
+
+
+def oracle_table_parallel(wl, planes=None, procs=None):
+    """The oracle's table (Algorithm "convgen", prescribed supports), its planes built in spawned
+    worker processes (every plane is computed independently of the others); `planes` limits
+    it to the planes a sample uses.  Host-side set-up of the CPU legs, never timed."""
+    import multiprocessing as mp
+
+    import oracle
+    K = wl.n_wplanes
+    todo = list(range(K)) if planes is None else sorted(int(k) for k in planes)
+    t = oracle.build_table(wl.du, K, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports, planes=())
+    procs = max(1, min(procs or (os.cpu_count() or 1), len(todo), 16))
+    chunks = [todo[i::procs] for i in range(procs)]
+    jobs = [(wl.du, K, wl.w_max, wl.oversample, wl.taper_support, list(wl.supports), c) for c in chunks if c]
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        parts = pool.map(_table_worker, jobs)
+    b2 = wl.oversample ** 2
+    for part in parts:
+        for k, (d, z) in part.items():
+            t.data[t.offsets[k]:t.offsets[k] + d.shape[0]] = d
+            t.zeta[k * b2:(k + 1) * b2] = z
+    return t
+
+
+def batch_grid_error(dev, plan, ot):
+    """Grid error of the batched configuration (8192^2, 64 planes, one polarisation) against the
+    FP64 oracle's plain gridding on its outer-w slice: 4 channels (331-350 MHz) x 24 steps x 300
+    baselines, reaching support 129 (the -m gpu parity test's slice)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1403_4209_gb300 as wg
+    import synth
+    bl, t0 = synth.outer_w_slice("batch_8k", n_times=24, n_top=100, n_spread=200)
+    wl = synth.make("batch_8k", baselines=bl, n_times=24, t_start=t0, n_chan=4, chan0=60)
+    tab = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
+    g = wg.Grid(wl.n_grid, wl.du, wl.n_pol, wl.n_chan, device=dev)
+    b = wg.VisBatch(torch.as_tensor(wl.uvw, device=dev), torch.as_tensor(wl.freq, device=dev), wl.vis.to(dev),
+                    wl.weight.to(dev), wl.flag.to(dev))
+    w = wg.WorkList(wl.rows * wl.n_chan, wl.n_chan, wl.n_pol)
+    wg.vis_compress(g, tab, b, w)
+    w.plan(tab, *plan)
+    wg.grid_vis(g, tab, w)
+    got = g.data.cpu().numpy()
+    del g, b, w, tab
+    torch.cuda.empty_cache()
+    f = wl.flag.numpy()
+    pl = oracle.place(wl.uvw, wl.freq, wl.du, wl.n_grid, ot, flag=f)
+    ref = oracle.grid_plain(pl, ot, wl.vis.numpy(), wl.weight.numpy(), f, wl.n_grid)
+    S = pl.S[pl.griddable]
+    return {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "max_abs_over_max": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+            "reference": "FP64 oracle, plain gridding definition",
+            "sample": "batch_8k geometry, 4 channels (331-350 MHz) x 24 steps around the largest |w| x 300 "
+                      "baselines (100 with the largest |w|), %d records, supports %d..%d" % (
+                          wl.rows * wl.n_chan, int(S.min()), int(S.max()))}
 
 
 def run_batch(args, rank, world, local_rank):
@@ -621,7 +702,90 @@ def run_batch(args, rank, world, local_rank):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, world, dev)
-    value = whole_job_rate(total, ms, world)
+    value = whole_job_rate(real, ms, world)
+
+    # end to end through the public API (eager calls): every step copies uvw and each group's
+    # visibilities, weights and flags from pinned host memory and reads each group's Stokes-I
+    # images back.  Groups are double-buffered: group u + 1's inputs copy on a copy stream
+    # while group u computes.
+    e2e = None
+    if args.e2e_steps > 0:
+        del graph
+        torch.cuda.empty_cache()
+        h_uvw = torch.empty(uvw_d.shape, dtype=uvw_d.dtype, pin_memory=True)
+        h_uvw.copy_(uvw_d)
+        h_vis = [torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for v in wl.vis]
+        h_flag = [torch.empty(f.shape, dtype=f.dtype, pin_memory=True) for f in wl.flag]
+        for hv, hf, v, f in zip(h_vis, h_flag, wl.vis, wl.flag):
+            hv.copy_(v)
+            hf.copy_(f)
+        h_w = torch.empty(wl.weight[0].shape, dtype=torch.float32, pin_memory=True)
+        h_w.copy_(wl.weight[0])
+        h_img = [torch.empty(img[0:G].shape, dtype=img.dtype, pin_memory=True) for _ in range(2)]
+        uvw_s = [torch.empty_like(uvw_d) for _ in range(2)]
+        gslot = [(torch.empty_like(wl.vis[0]), torch.empty_like(wl.weight[0]), torch.empty_like(wl.flag[0]))
+                 for _ in range(2)]
+        freqs = [b.freq for _, b, _ in groups]
+        cstream = torch.cuda.Stream()
+        copied, consumed = [torch.cuda.Event() for _ in range(2)], [torch.cuda.Event() for _ in range(2)]
+        u_copied, u_consumed = [torch.cuda.Event() for _ in range(2)], [torch.cuda.Event() for _ in range(2)]
+        n_groups = len(groups)
+        h2d = h_uvw.numel() * 8 + sum(hv.numel() * 8 + hf.numel() + h_w.numel() * 4 for hv, hf in zip(h_vis, h_flag))
+        d2h = img.numel() * 4
+
+        def issue(u):
+            k, gi = divmod(u, n_groups)
+            with torch.cuda.stream(cstream):
+                if gi == 0:
+                    cstream.wait_event(u_consumed[k % 2])
+                    uvw_s[k % 2].copy_(h_uvw, non_blocking=True)
+                    u_copied[k % 2].record(cstream)
+                cstream.wait_event(consumed[u % 2])
+                v, w_, f_ = gslot[u % 2]
+                v.copy_(h_vis[gi], non_blocking=True)
+                w_.copy_(h_w, non_blocking=True)
+                f_.copy_(h_flag[gi], non_blocking=True)
+                copied[u % 2].record(cstream)
+
+        def e2e_steps(n):
+            for ev in consumed + u_consumed:
+                ev.record(stream)
+            issue(0)
+            for u in range(n * n_groups):
+                if u + 1 < n * n_groups:
+                    issue(u + 1)
+                k, gi = divmod(u, n_groups)
+                if gi == 0:
+                    stream.wait_event(u_copied[k % 2])
+                stream.wait_event(copied[u % 2])
+                (g, _, im), (seg, sl, fr) = groups[gi], plans[gi]
+                v, w_, f_ = gslot[u % 2]
+                bt = wg.VisBatch(uvw_s[k % 2], freqs[gi], v, w_, f_)
+                g.zero()
+                wlst.plan(tab, seg, sl, fr)
+                wg.vis_compress(g, tab, bt, wlst)
+                wg.grid_vis(g, tab, wlst)
+                wg.grid_correct(g, tab, mode=wg.IMAGE_STOKES_I, out=im)
+                h_img[u % 2].copy_(im, non_blocking=True)
+                consumed[u % 2].record(stream)
+                if gi == n_groups - 1:
+                    u_consumed[k % 2].record(stream)
+
+        e2e_steps(1)
+        torch.cuda.synchronize()
+        barrier(world)
+        x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        x0.record(stream)
+        e2e_steps(args.e2e_steps)
+        x1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(x0.elapsed_time(x1) / args.e2e_steps, world, dev)
+        e2e = {"value": round(whole_job_rate(real, ms_e2e, world), 3), "unit": UNIT,
+               "total_rate_G": round(whole_job_rate(total, ms_e2e, world), 3), "ms_per_step": round(ms_e2e, 3),
+               "steps": args.e2e_steps, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "pipelining": "channel groups double-buffered on a copy stream; eager calls (no graph)"}
+        del h_uvw, h_vis, h_flag, h_w, h_img, uvw_s, gslot
+        torch.cuda.synchronize()
     peaks, src = _peaks()
     props = torch.cuda.get_device_properties(local_rank)
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -632,7 +796,7 @@ def run_batch(args, rank, world, local_rank):
     line = {
         "metric": "gridding/degridding G grid-point updates/s and % roofline at stated grid error",
         "value": round(value, 3),
-        "unit": "G grid-point updates/s (total rate, whole step)",
+        "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -643,8 +807,8 @@ def run_batch(args, rank, world, local_rank):
                    "records_per_step": wl.rows * C, "input_bytes": int(in_bytes),
                    "l2": "inputs larger than L2 (no flush needed)", "chan_group": G,
                    "plans_seg_len_slots_fixed_r": plans, "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "rates": {"total_step_G": round(value, 3),
-                  "real_step_G": round(world * real / (ms * 1e-3) / 1e9, 3),
+        "rates": {"real_step_G": round(value, 3),
+                  "total_step_G": round(whole_job_rate(total, ms, world), 3),
                   "real_gridder_G": round(real / (t_grid * 1e-3) / 1e9, 3),
                   "total_gridder_G": round(total / (t_grid * 1e-3) / 1e9, 3),
                   "gridder_ms": round(t_grid, 3), "updates_real": real, "updates_total": total},
@@ -655,13 +819,15 @@ def run_batch(args, rank, world, local_rank):
                                     % (props.multi_processor_count, sm_mhz, src),
                      "traffic": None},
         "ceilings": measured_ceilings(real / (t_grid * 1e-3), wl.n_pol),
-        "e2e": None,
+        "e2e": e2e,
         "gpu_launches": int(captured * args.steps),
         "graph": {"captured_launches_per_step": int(captured), "replays": args.steps},
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_sample(args.workload, *CPU_SAMPLE[args.workload])
+        ot = oracle_table_parallel(wl)
+        line["cpu_baseline"] = cpu_sample(args.workload, *CPU_SAMPLE[args.workload], ot=ot)
+        line["grid_error"] = batch_grid_error(dev, plans[-1], ot)
     return line
 
 
@@ -740,17 +906,18 @@ def run_autograd(args, rank, world, local_rank):
     t_fwd, t_bwd = f0.elapsed_time(f1), b0.elapsed_time(b1)
     tot_f = st_f["updates"] + st_f["updates_saved"]
     tot_a = st_a["updates"] + st_a["updates_saved"]
-    value = whole_job_rate(tot_f + tot_a, ms, world)
+    value = whole_job_rate(st_f["updates"] + st_a["updates"], ms, world)
     line = {
         "metric": "gridding/degridding G grid-point updates/s and % roofline at stated grid error",
         "value": round(value, 3),
-        "unit": "G grid-point updates/s (total rate: forward degridding + backward gridding, whole step)",
+        "unit": "G grid-point updates/s (real rate: forward degridding + backward gridding, whole step)",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "%s: %s" % (args.workload, WORKLOADS[args.workload]),
                    "records_per_step": wl.rows * wl.n_chan, "l2": "inputs larger than L2 (no flush needed)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "rates": {"forward_ms": round(t_fwd, 3), "backward_ms": round(t_bwd, 3),
+                  "total_step_G": round(whole_job_rate(tot_f + tot_a, ms, world), 3),
                   "forward_total_G": round(tot_f / (t_fwd * 1e-3) / 1e9, 3),
                   "backward_total_G": round(tot_a / (t_bwd * 1e-3) / 1e9, 3),
                   "updates_total_forward": tot_f, "updates_total_backward": tot_a,
@@ -788,13 +955,15 @@ def cpu_sample_autograd(workload, n_chan, n_times):
                           workload, n_chan, n_times, wl.n_baselines, wl.rows * wl.n_chan)}
 
 
-def _oracle_setup(workload, chans, n_times):
+def _oracle_setup(workload, chans, n_times, ot=None):
     """Inputs (one channel each) and the oracle's table for the CPU sample (untimed)."""
     import oracle
     import synth
     base, _ = SYNTH_NAME.get(workload, (workload, {}))
     sets = [synth.make(base, n_chan=1, chan0=c, n_times=n_times) for c in chans]
     wl = sets[0]
+    if ot is not None:
+        return sets, ot
     if WSTACK.get(workload):
         from oracle.wstack import stacking_table
         K = WSTACK[workload]
@@ -805,8 +974,8 @@ def _oracle_setup(workload, chans, n_times):
 
 
 def _oracle_run(workload, wl, ot):
-    """The FP64 oracle (placement, compression, gridding) on a workload slice; returns (total
-    updates, start, end) on the host's monotonic clock."""
+    """The FP64 oracle (placement, compression, gridding) on a workload slice; returns (real
+    updates, total updates, start, end) on the host's monotonic clock."""
     import numpy as np
 
     import oracle
@@ -830,7 +999,7 @@ def _oracle_run(workload, wl, ot):
         oracle.grid_plain(pl, ot, vis, w, f, wl.n_grid)
     t1 = time.perf_counter()
     st = oracle.stats(pl, g, c)
-    return (st["updates"] + st["updates_saved"]) * wl.n_pol, t0, t1
+    return st["updates"] * wl.n_pol, (st["updates"] + st["updates_saved"]) * wl.n_pol, t0, t1
 
 
 def _oracle_proc(workload, chans, n_times, start, q):
@@ -845,7 +1014,7 @@ def _oracle_proc(workload, chans, n_times, start, q):
         q.put(_oracle_run(workload, wl, ot) + (wl.n_baselines, wl.rows))
 
 
-def cpu_sample(workload, n_chan, n_times, procs=1):
+def cpu_sample(workload, n_chan, n_times, procs=1, ot=None):
     """The FP64 oracle on a bounded sample of the same geometry: n_chan channels x n_times steps.
     procs > 1 spreads the channels over worker processes (spawned, so no CUDA state is
     inherited) that start their timed sections together; the all-core rate is all updates over
@@ -855,18 +1024,20 @@ def cpu_sample(workload, n_chan, n_times, procs=1):
         import synth
         wl = synth.make(workload, n_chan=n_chan, n_times=n_times)
         ot = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
-        upd, t0, t1 = _oracle_run(workload, wl, ot)
-        return {"value": round(upd / (t1 - t0) / 1e9, 4), "unit": "G grid-point updates/s (total rate)",
+        upd, tot, t0, t1 = _oracle_run(workload, wl, ot)
+        return {"value": round(upd / (t1 - t0) / 1e9, 4), "unit": UNIT,
+                "total_rate_G": round(tot / (t1 - t0) / 1e9, 4),
                 "cores": 1, "kind": "oracle", "seconds": round(t1 - t0, 2),
                 "sample": "%s geometry, %d interleaved channels x %d time steps x %d baselines (%d records), FP64 "
                           "oracle: placement + compression + gridding onto one grid, single thread" % (
                               workload, n_chan, n_times, wl.n_baselines, wl.rows * wl.n_chan)}
     if procs <= 1:
-        sets, ot = _oracle_setup(workload, range(n_chan), n_times)
+        sets, ot = _oracle_setup(workload, range(n_chan), n_times, ot)
         res = [_oracle_run(workload, wl, ot) for wl in sets]
         upd = sum(r[0] for r in res)
-        dt = sum(r[2] - r[1] for r in res)
-        return {"value": round(upd / dt / 1e9, 4), "unit": "G grid-point updates/s (total rate)",
+        tot = sum(r[1] for r in res)
+        dt = sum(r[3] - r[2] for r in res)
+        return {"value": round(upd / dt / 1e9, 4), "unit": UNIT, "total_rate_G": round(tot / dt / 1e9, 4),
                 "cores": 1, "kind": "oracle", "seconds": round(dt, 2),
                 "sample": "%s geometry, %d channels x %d time steps x %d baselines (%d records), FP64 oracle: "
                           "placement + compression + gridding, single thread" % (
@@ -883,13 +1054,14 @@ def cpu_sample(workload, n_chan, n_times, procs=1):
     for p in ps:
         p.join(60)
     upd = sum(r[0] for r in res)
-    span = max(r[2] for r in res) - min(r[1] for r in res)
-    single = sum(r[0] / (r[2] - r[1]) for r in res) / len(res)
-    return {"value": round(upd / span / 1e9, 4), "unit": "G grid-point updates/s (total rate)", "cores": procs,
-            "kind": "oracle", "seconds": round(span, 2), "single_core_value": round(single / 1e9, 4),
+    tot = sum(r[1] for r in res)
+    span = max(r[3] for r in res) - min(r[2] for r in res)
+    single = sum(r[0] / (r[3] - r[2]) for r in res) / len(res)
+    return {"value": round(upd / span / 1e9, 4), "unit": UNIT, "total_rate_G": round(tot / span / 1e9, 4),
+            "cores": procs, "kind": "oracle", "seconds": round(span, 2), "single_core_value": round(single / 1e9, 4),
             "sample": "%s geometry, %d channels x %d time steps x %d baselines (%d records), FP64 oracle: "
                       "placement + compression + gridding, channels spread over %d processes" % (
-                          workload, n_chan, n_times, res[0][3], sum(r[4] for r in res), procs)}
+                          workload, n_chan, n_times, res[0][4], sum(r[5] for r in res), procs)}
 
 
 def grid_error_sample(workload, dev, plan, interleave=False, stack_k=0):
@@ -933,6 +1105,57 @@ def grid_error_sample(workload, dev, plan, interleave=False, stack_k=0):
                                                                                       wl.rows * wl.n_chan)}
 
 
+def variant_errors(dev, plan):
+    """Grid error against the FP64 oracle (the plain definition, eq. "gridding"; the whole
+    channel through the oracle's compressed gridding, equal to it up to rounding) of the plain
+    FP32 path and of every precision variant, on two inputs of the wproj_2k geometry: the
+    300-baseline x 24-step x 2-channel slice, and the whole of channel 15 (180 MHz: 2016
+    baselines x 3600 steps, 7.26 M records), where a pixel takes many flushes.  The gridder
+    runs under the benchmark's plan."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1403_4209_gb300 as wg
+    import synth
+    out = {}
+    ot = None
+    for cname, kw in (("slice", dict(n_chan=2, n_times=24, n_baselines=300)), ("channel15", dict(n_chan=1, chan0=15))):
+        wl = synth.make("wproj_2k", **kw)
+        if ot is None:      # slices share the full workload's cell size and w_max, hence the table
+            ot = oracle.build_table(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support,
+                                    supports=wl.supports)
+        vis, w, f = wl.vis.numpy(), wl.weight.numpy(), wl.flag.numpy()
+        pl = oracle.place(wl.uvw, wl.freq, wl.du, wl.n_grid, ot, flag=f)
+        ref = (oracle.grid_plain if cname == "slice" else oracle.grid_compressed)(pl, ot, vis, w, f, wl.n_grid)
+        nref, mref = np.linalg.norm(ref), np.max(np.abs(ref))
+        uvw_d, freq_d = torch.as_tensor(wl.uvw, device=dev), torch.as_tensor(wl.freq, device=dev)
+        vis_d = wl.vis.to(dev)
+        vis_h, scale_h = synth.to_half_vis(vis_d)
+        b32 = wg.VisBatch(uvw_d, freq_d, vis_d, wl.weight.to(dev), wl.flag.to(dev))
+        b16 = wg.VisBatch(uvw_d, freq_d, vis_h, b32.weight, b32.flag, vis_scale=scale_h)
+        wlst = wg.WorkList(wl.rows * wl.n_chan, wl.n_chan, wl.n_pol)
+        for name, store, half, comp in (("fp32", "f32", False, False),) + VARIANTS:
+            tab = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support,
+                                     supports=wl.supports, store=store)
+            g = wg.Grid(wl.n_grid, wl.du, wl.n_pol, wl.n_chan, device=dev, compensated=comp)
+            wg.vis_compress(g, tab, b16 if half else b32, wlst)
+            wlst.plan(tab, *plan)
+            wg.grid_vis(g, tab, wlst)
+            d = g.data.cpu().numpy() - ref
+            out.setdefault(name, {})[cname] = {"rel_l2": float(np.linalg.norm(d) / nref),
+                                               "max_abs_over_max": float(np.max(np.abs(d)) / mref)}
+            del tab, g, d
+        del wlst, b32, b16, vis_d, vis_h
+        torch.cuda.empty_cache()
+    samples = {"slice": "wproj_2k geometry, 300 baselines x 24 steps x 2 channels (14400 records)",
+               "channel15": "wproj_2k geometry, channel 15 (180 MHz), 2016 baselines x 3600 steps (7257600 records)"}
+    for v in out.values():
+        v["reference"] = "FP64 oracle"
+        v["samples"] = samples
+    return out
+
+
 def run_reference(args):
     """The oracle as the reference arm: each step one bounded sample on the host cores."""
     import numpy as np
@@ -961,9 +1184,10 @@ def run_reference(args):
     for _ in range(args.steps):
         st = step()
     dt = (time.perf_counter() - t0) / args.steps
+    real = st["updates"] * wl.n_pol
     total = (st["updates"] + st["updates_saved"]) * wl.n_pol
-    value = total / dt / 1e9
-    unit = "G grid-point updates/s (total rate, whole step)"
+    value = real / dt / 1e9
+    unit = UNIT
     sample = ("%s geometry, %d channels x %d time steps x %d baselines (%d records) per step" %
               (args.workload, n_chan, n_times, wl.n_baselines, wl.rows * wl.n_chan))
     return {
@@ -975,6 +1199,7 @@ def run_reference(args):
         "config": {"workload": "%s: %s%s" % (args.workload, WORKLOADS[args.workload],
                                               "" if args.n_chan is None and args.n_times is None else
                                               " (slice: %s channels, %s steps)" % (args.n_chan, args.n_times)), "sample": sample},
+        "rates": {"total_rate_G": round(total / dt / 1e9, 4), "updates_real": real, "updates_total": total},
         "cpu_baseline": {"value": round(value, 4), "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 4), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -1063,6 +1288,12 @@ def main():
     ap.add_argument("--n-chan", type=int, default=None, help="run a slice: first n channels (profiling)")
     ap.add_argument("--n-times", type=int, default=None, help="run a slice: n time steps (profiling)")
     ap.add_argument("--chan0", type=int, default=0, help="first channel of an --n-chan slice")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched 8192^2 section that the default wproj_2k run adds under 'batch_8k'")
+    ap.add_argument("--batch-steps", type=int, default=5,
+                    help="timed steps of that section (at most --steps; about 2.4 s each)")
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="end-to-end steps of the batched workload (0: skip)")
     ap.add_argument("--sweep", choices=sorted(SWEEPS) + ["all"], default=None,
                     help="instead of the benchmark line, the rate sweeps of the thesis's experiment batches 2-4 "
                          "(one JSON line per point)")
@@ -1086,6 +1317,18 @@ def main():
         torch.distributed.init_process_group("nccl")
     runner = run_batch if args.workload in CHAN_GROUP else run_autograd if args.workload == "degrid_1k" else run_ours
     line = runner(args, rank, world, local_rank)
+    if args.workload == "wproj_2k" and args.n_chan is None and args.n_times is None and not args.no_batch:
+        # the batched configuration (8192^2 grids, 64 channels, 64 planes, one graph per step) at
+        # full size, reported beside the headline under its own key with its own measurements
+        import copy
+
+        import torch
+        torch.cuda.empty_cache()
+        b_args = copy.copy(args)
+        b_args.workload = "batch_8k"
+        b_args.steps = max(1, min(args.steps, args.batch_steps))
+        b_args.warmup = 3
+        line["batch_8k"] = run_batch(b_args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
