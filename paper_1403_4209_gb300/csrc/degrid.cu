@@ -134,9 +134,10 @@ __device__ __forceinline__ int degrid_records(int j, int e1, int key, int S, int
         __syncwarp();
     };
     f32x2 pv[kRMax][P];
-    int toff[kRMax], cur[kRMax];     // sample offset and pixel held of each owned class
+    int toff[kRMax], cur[kRMax];     // sample byte offset and pixel held of each owned class
     unsigned valid = 0;
     const int s2 = S * S, sbase = blk * 32 * R;
+    const float inv_s = 1.0f / (float)S;
 #pragma unroll
     for (int r = 0; r < kRMax; ++r) {
         const int sl = sbase + r * 32 + lane;
@@ -144,8 +145,8 @@ __device__ __forceinline__ int degrid_records(int j, int e1, int key, int S, int
         toff[r] = 0;
         if (r < R && sl < s2) {
             valid |= 1u << r;
-            const int q = sl / S;
-            sm.puv[r][lane] = (sl - q * S) | (q << 16);
+            const int2 vu = divmod_small(sl, S, inv_s);      // (pv, pu)
+            sm.puv[r][lane] = vu.y | (vu.x << 16);
         }
 #pragma unroll
         for (int p = 0; p < P; ++p) pv[r][p] = 0ull;
@@ -165,7 +166,7 @@ __device__ __forceinline__ int degrid_records(int j, int e1, int key, int S, int
                     du -= (du >= S) ? S : 0;
                     int dv = (puv >> 16) + cv;
                     dv -= (dv >= S) ? S : 0;
-                    toff[r] = dv * S + du;
+                    toff[r] = (dv * S + du) * (int)sizeof(float2);
                     const int pix = (y0 + dv) * N + x0 + du;
                     if (pix != cur[r]) {
                         load_pixel<P>(gch + (size_t)pix * P, pv[r]);
@@ -180,7 +181,8 @@ __device__ __forceinline__ int degrid_records(int j, int e1, int key, int S, int
 #pragma unroll
         for (int r = 0; r < kRMax; ++r) {
             if (RT == 0 && r >= R) break;
-            if (r < R) kv[r] = __ldg(kz + toff[r]);
+            // unsigned 32-bit byte offset: cheaper than a signed element index (see the gridder)
+            if (r < R) kv[r] = __ldg(reinterpret_cast<const f32x2*>(reinterpret_cast<const char*>(kz) + (unsigned)toff[r]));
         }
         // A_p = sum kx (gx, gy), B_p = sum ky (gx, gy); conj(k) g = (A.x + B.y, A.y - B.x)
         f32x2 A[P], B[P];

@@ -16,6 +16,8 @@
 // its offsets with the modular wrap and flushes the pixels that changed.  The segment's entries
 // and weighted visibilities are staged in shared memory once per task (cp.async).  R (points per
 // lane) is chosen per run of records with the same support and channel, or fixed per launch.
+#include <type_traits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -112,6 +114,18 @@ __device__ __forceinline__ TS load_sample(const TS* p)
 __device__ __forceinline__ f32x2 load_kv(const float2* p) { return __ldg(reinterpret_cast<const f32x2*>(p)); }
 template <typename TS>
 __device__ __forceinline__ TS load_kv(const TS* p) { return load_sample(p); }
+// A point's sample offset: in bytes for FP32 samples, added to the sub-kernel's address as an
+// unsigned 32-bit value (as a signed element index it measured about two integer instructions
+// more per load); in elements for the 4-byte samples, where the element form measured faster.
+template <typename TS>
+constexpr int kOffScale = std::is_same<TS, float2>::value ? (int)sizeof(float2) : 1;
+__device__ __forceinline__ f32x2 load_at(const float2* kz, int off)
+{
+    return load_kv(reinterpret_cast<const float2*>(reinterpret_cast<const char*>(kz) + (unsigned)off));
+}
+template <typename TS>
+__device__ __forceinline__ TS load_at(const TS* kz, int off) { return load_kv(kz + off); }
+
 template <typename TS>
 struct KvReg { typedef TS type; };
 template <>
@@ -210,9 +224,13 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
     typedef typename KvReg<TS>::type KV;
     if constexpr (RT > 0) R = RT;
     f32x2 acc[kRMax][P][KA];
-    int toff[kRMax];
+    int toff[kRMax];         // each point's sample offset in the sub-kernel (kOffScale units)
     unsigned valid = 0;
     const int s2 = S * S, sbase = blk * 32 * R;
+    // slots run row-major over the residue classes, so the 32 lanes of a point-row read
+    // consecutive samples (a layout of 4 x 8 class blocks per point-row, which wraps fewer
+    // point-rows per footprint move, spread each load over more cache lines and measured slower)
+    const float inv_s = 1.0f / (float)S;
 #pragma unroll
     for (int r = 0; r < kRMax; ++r) {
         const int sl = sbase + r * 32 + lane;
@@ -220,8 +238,8 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
         toff[r] = 0;
         if (r < R && sl < s2) {
             valid |= 1u << r;
-            const int pv = sl / S;
-            sm.puv[r][lane] = (sl - pv * S) | (pv << 16);
+            const int2 vu = divmod_small(sl, S, inv_s);      // (pv, pu)
+            sm.puv[r][lane] = vu.y | (vu.x << 16);
         }
 #pragma unroll
         for (int p = 0; p < P; ++p)
@@ -243,7 +261,7 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
                     du -= (du >= S) ? S : 0;
                     int dv = (puv >> 16) + cv;
                     dv -= (dv >= S) ? S : 0;
-                    toff[r] = dv * S + du;
+                    toff[r] = (dv * S + du) * kOffScale<TS>;
                     const int pix = (y0 + dv) * N + x0 + du;
                     const int cur = sm.cur[r][lane];
                     if (pix != cur) {
@@ -259,7 +277,7 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
 #pragma unroll
         for (int r = 0; r < kRMax; ++r) {
             if (RT == 0 && r >= R) break;
-            if (r < R) kv[r] = load_kv(kz + toff[r]);   // invalid points read offset 0, never flushed
+            if (r < R) kv[r] = load_at(kz, toff[r]);   // invalid points read offset 0, never flushed
         }
         if constexpr (KA == 2) {
             // A += k (gx, gx), B += k (gy, gy)
@@ -305,8 +323,10 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
     }
 #pragma unroll
     for (int r = 0; r < kRMax; ++r) {
-        const int cur = sm.cur[r][lane];
-        if (cur >= 0) flush_pixel<P, COMP>(gch, ech, cur, acc[r]);
+        if (r < R) {     // points past R hold no pixel
+            const int cur = sm.cur[r][lane];
+            if (cur >= 0) flush_pixel<P, COMP>(gch, ech, cur, acc[r]);
+        }
     }
     return j;
 }

@@ -185,6 +185,18 @@ __device__ __forceinline__ double pswf_eval_dev(const double* a, int n, double x
     return s;
 }
 
+// (a / d, a mod d) for 0 <= a < 2^22 and 1 <= d < 2^12, inv_d = 1.0f / d: the truncated float
+// quotient is within one of the integer quotient, and one correction step each way makes it
+// exact (a few instructions against about twenty for an integer division by a runtime divisor)
+__device__ __forceinline__ int2 divmod_small(int a, int d, float inv_d)
+{
+    int q = __float2int_rz((float)a * inv_d);
+    int m = a - q * d;
+    if (m < 0) { --q; m += d; }
+    if (m >= d) { ++q; m -= d; }
+    return make_int2(q, m);
+}
+
 // prolate spheroidal psi_0(c, x) as even Legendre coefficients (host eigen-solver)
 std::vector<double> pswf_coefficients(double c);
 double pswf_eval_host(const std::vector<double>& coef, double x);

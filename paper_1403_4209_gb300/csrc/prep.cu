@@ -42,16 +42,6 @@ __device__ __forceinline__ int mod_small(int a, int S, float inv_s)
     return r;
 }
 
-// (j / C, j % C) for 0 <= j < 2^20 and 1 <= C < 2^12, by the corrected float quotient
-__device__ __forceinline__ int2 divmod_small(int j, int C, float inv_c)
-{
-    int q = __float2int_rz((float)j * inv_c);
-    int r = j - q * C;
-    if (r < 0) { --q; r += C; }
-    if (r >= C) { ++q; r -= C; }
-    return make_int2(q, r);
-}
-
 // some polarisation of record rec unflagged; with `vec` (flag pointer aligned to P bytes) the P
 // flag bytes are read in one load and tested for a zero byte
 __device__ __forceinline__ bool any_unflagged(const uint8_t* __restrict__ flag, int64_t rec, int P, int vec)
