@@ -591,10 +591,10 @@ def oracle_table_parallel(wl, planes=None, procs=None):
     return t
 
 
-def batch_grid_error(dev, plan, ot):
+def batch_grid_error(dev, plan, ot, stores=("f32",)):
     """Grid error of the batched configuration (8192^2, 64 planes, one polarisation) against the
     FP64 oracle's plain gridding on its outer-w slice: 4 channels (331-350 MHz) x 24 steps x 300
-    baselines, reaching support 129 (the -m gpu parity test's slice)."""
+    baselines, reaching support 129 (the -m gpu parity test's slice), for each table store."""
     import numpy as np
     import torch
 
@@ -603,27 +603,31 @@ def batch_grid_error(dev, plan, ot):
     import synth
     bl, t0 = synth.outer_w_slice("batch_8k", n_times=24, n_top=100, n_spread=200)
     wl = synth.make("batch_8k", baselines=bl, n_times=24, t_start=t0, n_chan=4, chan0=60)
-    tab = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support, supports=wl.supports)
-    g = wg.Grid(wl.n_grid, wl.du, wl.n_pol, wl.n_chan, device=dev)
     b = wg.VisBatch(torch.as_tensor(wl.uvw, device=dev), torch.as_tensor(wl.freq, device=dev), wl.vis.to(dev),
                     wl.weight.to(dev), wl.flag.to(dev))
-    w = wg.WorkList(wl.rows * wl.n_chan, wl.n_chan, wl.n_pol)
-    wg.vis_compress(g, tab, b, w)
-    w.plan(tab, *plan)
-    wg.grid_vis(g, tab, w)
-    got = g.data.cpu().numpy()
-    del g, b, w, tab
-    torch.cuda.empty_cache()
+    got = {}
+    for store in stores:
+        tab = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support,
+                                 supports=wl.supports, store=store)
+        g = wg.Grid(wl.n_grid, wl.du, wl.n_pol, wl.n_chan, device=dev)
+        w = wg.WorkList(wl.rows * wl.n_chan, wl.n_chan, wl.n_pol)
+        wg.vis_compress(g, tab, b, w)
+        w.plan(tab, *plan)
+        wg.grid_vis(g, tab, w)
+        got[store] = g.data.cpu().numpy()
+        del g, w, tab
+        torch.cuda.empty_cache()
+    del b
     f = wl.flag.numpy()
     pl = oracle.place(wl.uvw, wl.freq, wl.du, wl.n_grid, ot, flag=f)
     ref = oracle.grid_plain(pl, ot, wl.vis.numpy(), wl.weight.numpy(), f, wl.n_grid)
     S = pl.S[pl.griddable]
-    return {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-            "max_abs_over_max": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
-            "reference": "FP64 oracle, plain gridding definition",
-            "sample": "batch_8k geometry, 4 channels (331-350 MHz) x 24 steps around the largest |w| x 300 "
-                      "baselines (100 with the largest |w|), %d records, supports %d..%d" % (
-                          wl.rows * wl.n_chan, int(S.min()), int(S.max()))}
+    sample = ("batch_8k geometry, 4 channels (331-350 MHz) x 24 steps around the largest |w| x 300 baselines "
+              "(100 with the largest |w|), %d records, supports %d..%d" % (wl.rows * wl.n_chan, int(S.min()), int(S.max())))
+    return {store: {"rel_l2": float(np.linalg.norm(v - ref) / np.linalg.norm(ref)),
+                    "max_abs_over_max": float(np.max(np.abs(v - ref)) / np.max(np.abs(ref))),
+                    "reference": "FP64 oracle, plain gridding definition", "sample": sample}
+            for store, v in got.items()}
 
 
 def run_batch(args, rank, world, local_rank):
@@ -703,6 +707,31 @@ def run_batch(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, world, dev)
     value = whole_job_rate(real, ms, world)
+
+    # the FP16 table at one polarisation: 4-byte samples halve the sample bytes the gridder
+    # fetches per update (eager, gridder time summed over the groups under the same plans)
+    variants = {}
+    if not args.no_variants:
+        tab16 = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support,
+                                   supports=wl.supports, store="f16")
+        t16 = 0.0
+        for (g, b, _), (seg, slots, fixed_r) in zip(groups, plans):
+            g.zero()
+            wlst.plan(tab16, seg, slots, fixed_r)
+            wg.vis_compress(g, tab16, b, wlst)
+            wg.grid_vis(g, tab16, wlst)           # warm-up of this group's launch
+            g.zero()
+            wg.vis_compress(g, tab16, b, wlst)
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            wg.grid_vis(g, tab16, wlst)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            t16 += v0.elapsed_time(v1)
+        variants["f16 table"] = {"gridder_ms": round(t16, 3), "real_gridder_G": round(real / (t16 * 1e-3) / 1e9, 3),
+                                 "total_gridder_G": round(total / (t16 * 1e-3) / 1e9, 3)}
+        del tab16
+        torch.cuda.empty_cache()
 
     # end to end through the public API (eager calls): every step copies uvw and each group's
     # visibilities, weights and flags from pinned host memory and reads each group's Stokes-I
@@ -820,6 +849,7 @@ def run_batch(args, rank, world, local_rank):
                      "traffic": None},
         "ceilings": measured_ceilings(real / (t_grid * 1e-3), wl.n_pol),
         "e2e": e2e,
+        "variants": variants,
         "gpu_launches": int(captured * args.steps),
         "graph": {"captured_launches_per_step": int(captured), "replays": args.steps},
         "clocks": clk,
@@ -827,7 +857,10 @@ def run_batch(args, rank, world, local_rank):
     if rank == 0 and not args.no_cpu_baseline:
         ot = oracle_table_parallel(wl)
         line["cpu_baseline"] = cpu_sample(args.workload, *CPU_SAMPLE[args.workload], ot=ot)
-        line["grid_error"] = batch_grid_error(dev, plans[-1], ot)
+        errs = batch_grid_error(dev, plans[-1], ot, stores=("f32",) + (("f16",) if variants else ()))
+        line["grid_error"] = errs["f32"]
+        if "f16" in errs:
+            variants["f16 table"]["grid_error"] = errs["f16"]
     return line
 
 

@@ -104,7 +104,7 @@ struct WorkList {
     bool interleave = false;              // last batch: channels interleaved onto one grid
     bool cross_swap = false;              // last batch: take-conjugate records swap cross hands
     int wstack_k = 1;                     // last batch: w-stacking planes (1: no stacking)
-    // per record
+    // per record (rinfo: placement, written for gridded records and each tile's first row)
     int4* rinfo = nullptr;
     uint8_t* rclass = nullptr;
     // per (tile, chan)
@@ -195,6 +195,45 @@ __device__ __forceinline__ int2 divmod_small(int a, int d, float inv_d)
     if (m < 0) { --q; m += d; }
     if (m >= d) { ++q; m -= d; }
     return make_int2(q, m);
+}
+
+// Exclusive scan of a[0..n) in place by the whole block (every thread calls it; blockDim a
+// multiple of 32, at most 1024), a[n] = the total; warp_tot is shared scratch of 32 ints.
+// Each thread sums a contiguous chunk, the chunk sums are scanned with warp shuffles and
+// the warp totals by the first warp, then each thread writes its chunk's prefixes.
+__device__ __forceinline__ void block_exclusive_scan(int* a, int n, int* warp_tot)
+{
+    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int ipt = (n + T - 1) / T;
+    const int b0 = min(n, t * ipt), b1 = min(n, b0 + ipt);
+    int s = 0;
+    for (int i = b0; i < b1; ++i) s += a[i];
+    int inc = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = T >> 5;
+        int v = (lane < nw) ? warp_tot[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane < nw) warp_tot[lane] = v;   // inclusive
+    }
+    __syncthreads();
+    int run = inc - s + (wid > 0 ? warp_tot[wid - 1] : 0);
+    for (int i = b0; i < b1; ++i) {
+        const int v = a[i];
+        a[i] = run;
+        run += v;
+    }
+    __syncthreads();
+    if (t == T - 1) a[n] = run;
+    __syncthreads();
 }
 
 // prolate spheroidal psi_0(c, x) as even Legendre coefficients (host eigen-solver)

@@ -211,43 +211,6 @@ __device__ __forceinline__ int nblk_of(int S, int slots)
     return (s2 + slots - 1) / slots;
 }
 
-// exclusive block scan of a[0..n) in place; a[n] = total.  Needs blockDim multiple of 32.
-__device__ void block_exclusive_scan(int* a, int n, int* warp_tot)
-{
-    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int ipt = (n + T - 1) / T;
-    const int b0 = min(n, t * ipt), b1 = min(n, b0 + ipt);
-    int s = 0;
-    for (int i = b0; i < b1; ++i) s += a[i];
-    int inc = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        int v = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += v;
-    }
-    if (lane == 31) warp_tot[wid] = inc;
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = T >> 5;
-        int v = (lane < nw) ? warp_tot[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            int u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += u;
-        }
-        if (lane < nw) warp_tot[lane] = v;   // inclusive
-    }
-    __syncthreads();
-    int run = inc - s + (wid > 0 ? warp_tot[wid - 1] : 0);
-    for (int i = b0; i < b1; ++i) {
-        int v = a[i];
-        a[i] = run;
-        run += v;
-    }
-    __syncthreads();
-    if (t == T - 1) a[n] = run + 0;
-    __syncthreads();
-    if (t == 0 && n > 0 && b1 < n) {}  // (all threads participated)
-}
-
 }  // namespace
 
 __global__ void k_chan_scale(const double* __restrict__ freq, int C, double beta_over_du, double* lam_inv,
@@ -362,7 +325,9 @@ __global__ void __launch_bounds__(512, 3) k_classify(const double* __restrict__ 
         const int gc = s_gc[j];
         const int rank = pp.interleave ? s_scan[j] - s_scan[0] : s_scan[ch * nrows + rr] - s_scan[ch * nrows];
         info.w |= ((gc & 1) << kBitG) | (((gc >> 1) & 1) << kBitC) | (rank << 16);
-        rinfo[rec] = info;
+        // k_compact reads the placement of gridded records and of the tile's first row (whose
+        // compressed records carry a run on from the previous tile): only those are written
+        if ((gc & 1) || j < C) rinfo[rec] = info;
         rclass[rec] = (uint8_t)gc;
     }
     for (int ch = threadIdx.x; ch < C; ch += blockDim.x)   // interleaved: one list, channel 0's
