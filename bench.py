@@ -673,10 +673,14 @@ def run_batch(args, rank, world, local_rank):
         torch.cuda.synchronize()
         t_grid += e0.elapsed_time(e1)
 
+    cur_plan = [wlst.plan_params]
+
     def step():
-        for (g, b, im), (seg, slots, fixed_r) in zip(groups, plans):
+        for (g, b, im), pl in zip(groups, plans):
             g.zero()
-            wlst.plan(tab, seg, slots, fixed_r)
+            if pl != cur_plan[0]:       # re-plan only when the group's plan differs from the last one
+                wlst.plan(tab, *pl)
+                cur_plan[0] = pl
             wg.vis_compress(g, tab, b, wlst)
             wg.grid_vis(g, tab, wlst)
             wg.grid_correct(g, tab, mode=wg.IMAGE_STOKES_I, out=im)
@@ -732,6 +736,7 @@ def run_batch(args, rank, world, local_rank):
                                  "total_gridder_G": round(total / (t16 * 1e-3) / 1e9, 3)}
         del tab16
         torch.cuda.empty_cache()
+        cur_plan[0] = wlst.plan_params
 
     # end to end through the public API (eager calls): every step copies uvw and each group's
     # visibilities, weights and flags from pinned host memory and reads each group's Stokes-I
@@ -791,7 +796,9 @@ def run_batch(args, rank, world, local_rank):
                 v, w_, f_ = gslot[u % 2]
                 bt = wg.VisBatch(uvw_s[k % 2], freqs[gi], v, w_, f_)
                 g.zero()
-                wlst.plan(tab, seg, sl, fr)
+                if (seg, sl, fr) != cur_plan[0]:
+                    wlst.plan(tab, seg, sl, fr)
+                    cur_plan[0] = (seg, sl, fr)
                 wg.vis_compress(g, tab, bt, wlst)
                 wg.grid_vis(g, tab, wlst)
                 wg.grid_correct(g, tab, mode=wg.IMAGE_STOKES_I, out=im)

@@ -676,10 +676,20 @@ __global__ void k_segments(const int4* __restrict__ entries, long long* __restri
 {
     const long long n = scal[0];
     if (blockIdx.x == 0 && threadIdx.x == 0) scal[2] = (n + seg_len - 1) / seg_len;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int k = entries[e].w & 0xFFF;
-        const int nb = (k < K) ? nblk_of(__ldg(&supports[k]), slots) : 1;
-        atomicMax(&seg_nblk[e / seg_len], nb);
+    // seg_len is a multiple of 32, so the 32 entries of a warp's chunk share one segment: the
+    // warp takes their maximum and one lane updates the segment
+    const int lane = threadIdx.x & 31;
+    const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long base = warp0 * 32; base < n; base += n_warps * 32) {
+        const long long e = base + lane;
+        int nb = 0;
+        if (e < n) {
+            const int k = entries[e].w & 0xFFF;
+            nb = (k < K) ? nblk_of(__ldg(&supports[k]), slots) : 1;
+        }
+        const int m = __reduce_max_sync(0xffffffffu, nb);
+        if (lane == 0) atomicMax(&seg_nblk[base / seg_len], m);
     }
 }
 
