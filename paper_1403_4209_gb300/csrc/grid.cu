@@ -41,13 +41,15 @@ struct StagedRec {
 // offsets from the warp's base.
 template <int P>
 struct WarpSmem {
-    int (*puv)[32];          // [kRMax][32] each lane's owned residue classes (pu | pv << 16)
+    short (*pu)[32];         // [kRMax][32] each lane's owned residue classes: x mod S
+    short (*pv)[32];         // [kRMax][32] and y mod S
     int (*cur)[32];          // [kRMax][32] each lane's current pixels (read when the footprint moves)
     StagedRec<P>* rec;       // [seg_len]
-    static constexpr size_t kFixed = 2 * kRMax * 32 * sizeof(int);
+    static constexpr size_t kFixed = 2 * kRMax * 32 * sizeof(short) + kRMax * 32 * sizeof(int);
     __device__ explicit WarpSmem(unsigned char* base)
-        : puv(reinterpret_cast<int (*)[32]>(base)),
-          cur(reinterpret_cast<int (*)[32]>(base) + kRMax),
+        : pu(reinterpret_cast<short (*)[32]>(base)),
+          pv(reinterpret_cast<short (*)[32]>(base) + kRMax),
+          cur(reinterpret_cast<int (*)[32]>(base + 2 * kRMax * 32 * sizeof(short))),
           rec(reinterpret_cast<StagedRec<P>*>(base + kFixed)) {}
     static constexpr size_t bytes(int seg_len) { return kFixed + (size_t)seg_len * sizeof(StagedRec<P>); }
 };
@@ -236,10 +238,18 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
         const int sl = sbase + r * 32 + lane;
         sm.cur[r][lane] = -1;
         toff[r] = 0;
-        if (r < R && sl < s2) {
-            valid |= 1u << r;
-            const int2 vu = divmod_small(sl, S, inv_s);      // (pv, pu)
-            sm.puv[r][lane] = vu.y | (vu.x << 16);
+        if (r < R) {
+            // a slot past S^2 follows class (0, 0): its sample offset stays inside the
+            // sub-kernel, and it is never flushed
+            int pu = 0, pv = 0;
+            if (sl < s2) {
+                valid |= 1u << r;
+                const int2 vu = divmod_small(sl, S, inv_s);
+                pv = vu.x;
+                pu = vu.y;
+            }
+            sm.pu[r][lane] = (short)pu;
+            sm.pv[r][lane] = (short)pv;
         }
 #pragma unroll
         for (int p = 0; p < P; ++p)
@@ -253,20 +263,52 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
         if (E.x != fp) {     // the footprint moved: new offsets, flush the pixels that change
             const int x0 = E.x & 0xFFFF, y0 = (E.x >> 16) & 0xFFFF;
             const int cu = E.y & 0xFFFF, cv = (E.y >> 16) & 0xFFFF;
+            const int dx = x0 - (fp & 0xFFFF), dy = y0 - (fp >> 16);
+            if (fp >= 0 && ((dy == 0 && (dx == 1 || dx == -1)) || (dx == 0 && (dy == 1 || dy == -1)))) {
+                // A one-cell move (almost every move of a track).  Every point's offset shifts by
+                // the move; only the column (or row) of classes that left the footprint wraps to
+                // its other side, and only its points change pixel.  That class is the new
+                // origin's residue, one less for a move towards +x (+y).
+                const bool along_x = dy == 0;
+                const int d = along_x ? dx : dy;
+                const int cn = along_x ? cu : cv;                  // (-origin) mod S
+                const int m = cn ? S - cn : 0;                     // origin mod S
+                const int c = d > 0 ? (m ? m - 1 : S - 1) : m;     // the class that wraps
+                const int step = along_x ? 1 : S;                  // samples per cell of the move
+                const int shift = d * step * kOffScale<TS>;
+                const int wrap = d * S * step * kOffScale<TS>;
+                const int pstep = along_x ? d * S : d * S * N;     // pixel step of a wrapped point
+                short (*cls)[32] = along_x ? sm.pu : sm.pv;
 #pragma unroll
-            for (int r = 0; r < kRMax; ++r) {
-                if (r < R && (valid & (1u << r))) {
-                    const int puv = sm.puv[r][lane];
-                    int du = (puv & 0xFFFF) + cu;
-                    du -= (du >= S) ? S : 0;
-                    int dv = (puv >> 16) + cv;
-                    dv -= (dv >= S) ? S : 0;
-                    toff[r] = (dv * S + du) * kOffScale<TS>;
-                    const int pix = (y0 + dv) * N + x0 + du;
-                    const int cur = sm.cur[r][lane];
-                    if (pix != cur) {
-                        if (cur >= 0) flush_pixel<P, COMP>(gch, ech, cur, acc[r]);
-                        sm.cur[r][lane] = pix;
+                for (int r = 0; r < kRMax; ++r) {
+                    if (r < R) {
+                        const bool w = cls[r][lane] == c;
+                        toff[r] += w ? wrap - shift : -shift;
+                        if (w && (valid & (1u << r))) {
+                            const int cur = sm.cur[r][lane];
+                            flush_pixel<P, COMP>(gch, ech, cur, acc[r]);
+                            sm.cur[r][lane] = cur + pstep;
+                        }
+                    }
+                }
+            } else {
+                // the first record of the run, or a jump: place every point from its class
+#pragma unroll
+                for (int r = 0; r < kRMax; ++r) {
+                    if (r < R) {
+                        int du = sm.pu[r][lane] + cu;
+                        du -= (du >= S) ? S : 0;
+                        int dv = sm.pv[r][lane] + cv;
+                        dv -= (dv >= S) ? S : 0;
+                        toff[r] = (dv * S + du) * kOffScale<TS>;
+                        if (valid & (1u << r)) {
+                            const int pix = (y0 + dv) * N + x0 + du;
+                            const int cur = sm.cur[r][lane];
+                            if (pix != cur) {
+                                if (cur >= 0) flush_pixel<P, COMP>(gch, ech, cur, acc[r]);
+                                sm.cur[r][lane] = pix;
+                            }
+                        }
                     }
                 }
             }
@@ -334,7 +376,8 @@ __device__ __forceinline__ int run_records(int j, int e1, int key, int S, int R,
 }  // namespace
 
 template <int P, typename TS, bool COMP, int RT>
-__global__ void __launch_bounds__(kWarps * 32, 4) k_grid(const int4* __restrict__ entries,
+// five blocks of 4 warps per SM at one polarisation (at most 102 registers), four otherwise
+__global__ void __launch_bounds__(kWarps * 32, P == 1 ? 5 : 4) k_grid(const int4* __restrict__ entries,
                                                          const float2* __restrict__ gamma,
                                                          const int* __restrict__ seg_off,
                                                          const long long* __restrict__ scal,
