@@ -394,6 +394,9 @@ def run_ours(args, rank, world, local_rank):
         tot += c1 - c0
         hid += max(0.0, min(c1, s1) - max(c0, s0))
     copy_hidden = hid / tot if tot > 0 else None
+    # mean durations of a copy and of a step while both streams run
+    copy_ms_ov = statistics.mean(a.elapsed_time(b) for a, b in tl_c[1:])
+    step_ms_ov = statistics.mean(a.elapsed_time(b) for a, b in tl_s)
     # the host-to-device copies alone (the link's share of the end-to-end step)
     c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     c0.record(cstream)
@@ -412,6 +415,7 @@ def run_ours(args, rank, world, local_rank):
            "d2h_bytes_per_step": int(d2h), "h2d_alone_ms": round(ms_h2d, 3),
            "h2d_gbs": round(h2d / (ms_h2d * 1e-3) / 1e9, 1),
            "copy_hidden_frac": None if copy_hidden is None else round(copy_hidden, 3),
+           "copy_ms_overlapped": round(copy_ms_ov, 3), "step_ms_overlapped": round(step_ms_ov, 3),
            "pipelining": "inputs double-buffered on a copy stream"}
     del slots, h_uvw, h_vis, h_w, h_f, h_img
     torch.cuda.synchronize()

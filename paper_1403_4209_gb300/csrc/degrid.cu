@@ -91,13 +91,15 @@ constexpr int kRedFloats = 64 * 33;      // per warp, any P
 // Per-warp shared memory: the residue-class arrays, the reduction buffer, then the segment's
 // staged entries.
 struct WarpSmem {
-    int (*puv)[32];          // [kRMax][32] each lane's owned residue classes (pu | pv << 16)
+    short (*pu)[32];         // [kRMax][32] each lane's owned residue classes: x mod S
+    short (*pv)[32];         // [kRMax][32] and y mod S
     float* red;              // [kRedFloats]
     int4* rec;               // [seg_len] entries, w replaced by the key
-    static constexpr size_t kFixed = kRMax * 32 * sizeof(int) + kRedFloats * sizeof(float);
+    static constexpr size_t kFixed = 2 * kRMax * 32 * sizeof(short) + kRedFloats * sizeof(float);
     __device__ explicit WarpSmem(unsigned char* base)
-        : puv(reinterpret_cast<int (*)[32]>(base)),
-          red(reinterpret_cast<float*>(base + kRMax * 32 * sizeof(int))),
+        : pu(reinterpret_cast<short (*)[32]>(base)),
+          pv(reinterpret_cast<short (*)[32]>(base) + kRMax),
+          red(reinterpret_cast<float*>(base + 2 * kRMax * 32 * sizeof(short))),
           rec(reinterpret_cast<int4*>(base + kFixed)) {}
     static constexpr size_t bytes(int seg_len) { return kFixed + (size_t)seg_len * sizeof(int4); }
 };
@@ -143,10 +145,18 @@ __device__ __forceinline__ int degrid_records(int j, int e1, int key, int S, int
         const int sl = sbase + r * 32 + lane;
         cur[r] = -1;
         toff[r] = 0;
-        if (r < R && sl < s2) {
-            valid |= 1u << r;
-            const int2 vu = divmod_small(sl, S, inv_s);      // (pv, pu)
-            sm.puv[r][lane] = vu.y | (vu.x << 16);
+        if (r < R) {
+            // a slot past S^2 follows class (0, 0): its sample offset stays inside the
+            // sub-kernel, and its pixel value stays 0
+            int pu = 0, pv_ = 0;
+            if (sl < s2) {
+                valid |= 1u << r;
+                const int2 vu = divmod_small(sl, S, inv_s);
+                pv_ = vu.x;
+                pu = vu.y;
+            }
+            sm.pu[r][lane] = (short)pu;
+            sm.pv[r][lane] = (short)pv_;
         }
 #pragma unroll
         for (int p = 0; p < P; ++p) pv[r][p] = 0ull;
@@ -158,19 +168,48 @@ __device__ __forceinline__ int degrid_records(int j, int e1, int key, int S, int
         if (E.x != fp) {     // the footprint moved: new offsets, reload the pixels that change
             const int x0 = E.x & 0xFFFF, y0 = (E.x >> 16) & 0xFFFF;
             const int cu = E.y & 0xFFFF, cv = (E.y >> 16) & 0xFFFF;
+            const int dx = x0 - (fp & 0xFFFF), dy = y0 - (fp >> 16);
+            if (fp >= 0 && ((dy == 0 && (dx == 1 || dx == -1)) || (dx == 0 && (dy == 1 || dy == -1)))) {
+                // a one-cell move: every offset shifts by the move, and only the class column
+                // (or row) that left the footprint wraps and takes a new pixel (as in the gridder)
+                const bool along_x = dy == 0;
+                const int d = along_x ? dx : dy;
+                const int cn = along_x ? cu : cv;                  // (-origin) mod S
+                const int m = cn ? S - cn : 0;                     // origin mod S
+                const int c = d > 0 ? (m ? m - 1 : S - 1) : m;     // the class that wraps
+                const int step = along_x ? 1 : S;
+                const int shift = d * step * (int)sizeof(float2);
+                const int wrap = d * S * step * (int)sizeof(float2);
+                const int pstep = along_x ? d * S : d * S * N;
+                short (*cls)[32] = along_x ? sm.pu : sm.pv;
 #pragma unroll
-            for (int r = 0; r < kRMax; ++r) {
-                if (r < R && (valid & (1u << r))) {
-                    const int puv = sm.puv[r][lane];
-                    int du = (puv & 0xFFFF) + cu;
-                    du -= (du >= S) ? S : 0;
-                    int dv = (puv >> 16) + cv;
-                    dv -= (dv >= S) ? S : 0;
-                    toff[r] = (dv * S + du) * (int)sizeof(float2);
-                    const int pix = (y0 + dv) * N + x0 + du;
-                    if (pix != cur[r]) {
-                        load_pixel<P>(gch + (size_t)pix * P, pv[r]);
-                        cur[r] = pix;
+                for (int r = 0; r < kRMax; ++r) {
+                    if (r < R) {
+                        const bool w = cls[r][lane] == c;
+                        toff[r] += w ? wrap - shift : -shift;
+                        if (w && (valid & (1u << r))) {
+                            cur[r] += pstep;
+                            load_pixel<P>(gch + (size_t)cur[r] * P, pv[r]);
+                        }
+                    }
+                }
+            } else {
+                // the first entry of the run, or a jump: place every point from its class
+#pragma unroll
+                for (int r = 0; r < kRMax; ++r) {
+                    if (r < R) {
+                        int du = sm.pu[r][lane] + cu;
+                        du -= (du >= S) ? S : 0;
+                        int dv = sm.pv[r][lane] + cv;
+                        dv -= (dv >= S) ? S : 0;
+                        toff[r] = (dv * S + du) * (int)sizeof(float2);
+                        if (valid & (1u << r)) {
+                            const int pix = (y0 + dv) * N + x0 + du;
+                            if (pix != cur[r]) {
+                                load_pixel<P>(gch + (size_t)pix * P, pv[r]);
+                                cur[r] = pix;
+                            }
+                        }
                     }
                 }
             }
@@ -255,7 +294,7 @@ __global__ void k_degrid_zero(float4* __restrict__ acc, const long long* __restr
 }
 
 template <int P, int RT>
-__global__ void __launch_bounds__(kWarps * 32, 4) k_degrid_sum(const int4* __restrict__ entries,
+__global__ void __launch_bounds__(kWarps * 32, P == 1 ? 5 : 4) k_degrid_sum(const int4* __restrict__ entries,
                                                                const int* __restrict__ seg_off,
                                                                const long long* __restrict__ scal,
                                                                const int* __restrict__ supports,
