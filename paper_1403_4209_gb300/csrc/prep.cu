@@ -379,17 +379,25 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int* __restrict__ tile_cnt,
 }
 
 __global__ void k_finalize(int* __restrict__ chan_base, int C, const unsigned long long* __restrict__ stat_priv,
-                           unsigned long long* __restrict__ stats, long long* __restrict__ scal)
+                           unsigned long long* __restrict__ stats, long long* __restrict__ scal, long long cap)
 {
     if (threadIdx.x == 0) {
+        // channel bases and the entry count, held to the work list's capacity (never reached
+        // with consistent counts; a count past it is reported as dropped)
         long long run = 0;
+        bool over = false;
         for (int c = 0; c < C; ++c) {
             const int t = chan_base[c];
             chan_base[c] = (int)run;
             run += t;
+            if (t < 0 || run > cap) {
+                over = true;
+                run = t < 0 ? run - t : cap;
+            }
         }
         chan_base[C] = (int)run;
         scal[0] = run;
+        if (over) atomicAdd(reinterpret_cast<unsigned long long*>(&scal[3]), 1ull);
     }
     for (int q = threadIdx.x; q < ST_TASKS; q += blockDim.x) {
         unsigned long long s = 0;
@@ -821,7 +829,7 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
     }
     k_scan_tiles<<<C, 1024, 0, s>>>(wl.tile_cnt, n_tiles, C, wl.chan_base);
     WG_LAUNCHED("k_scan_tiles");
-    k_finalize<<<1, 256, 0, s>>>(wl.chan_base, C, wl.stat_priv, wl.stats, wl.scal);
+    k_finalize<<<1, 256, 0, s>>>(wl.chan_base, C, wl.stat_priv, wl.stats, wl.scal, wl.cap);
     WG_LAUNCHED("k_finalize");
     if (rows > 0) {
         const size_t sm = compact_smem(rpb, C, P);
