@@ -54,8 +54,9 @@ WORKLOADS = {
                  "4 channels 120-180 MHz, 16 sqrt(w)-spaced w-planes, supports 9..33, beta=8, compression on",
     "batch_8k": "256 stations (10 km log-radial), 32640 baselines x 1800 steps at 2 s, 64 channels 50-350 MHz, "
                 "1 pol, complex64; grid 8192^2 x 64 ch; 64 sqrt(w)-spaced w-planes, supports 9..129; beta=8; "
-                "FP32 table; compression on; 8 groups of 8 channels through one reused work list, the whole "
-                "step captured in one CUDA graph, gridder plan autotuned per group",
+                "FP32 table; compression on; 8 groups of 8 channels prepared one after another into one work "
+                "list (WG_PREP_APPEND), one persistent gridder launch over all 64 channels, the whole step "
+                "captured in one CUDA graph, gridder plan autotuned on the appended batch",
 }
 # the unit of `value` and `e2e` in both arms (the driver divides one arm's value by the other's)
 UNIT = "G grid-point updates/s (real rate: updates the gridder performs, whole step)"
@@ -635,9 +636,10 @@ def batch_grid_error(dev, plan, ot, stores=("f32",)):
 
 
 def run_batch(args, rank, world, local_rank):
-    """Batching at scale: channel groups gridded into channel slices of one grid through one
-    reused work list, the whole step (every group's zeroing, preparation, re-plan, gridding and
-    finaliser) captured once in a CUDA graph and replayed."""
+    """Batching at scale: every channel group is prepared into one work list (WG_PREP_APPEND)
+    onto its channel slice of one grid, then one persistent gridder launch grids every
+    channel and one finaliser call makes the Stokes-I images.  The whole step is captured once
+    in a CUDA graph and replayed."""
     import torch
 
     import paper_1403_4209_gb300 as wg
@@ -653,41 +655,68 @@ def run_batch(args, rank, world, local_rank):
     full = torch.zeros((C, N, N, P), dtype=torch.complex64, device=dev)
     img = torch.empty((C, N, N), dtype=torch.float32, device=dev)
     uvw_d = torch.as_tensor(wl.uvw, device=dev)
-    groups = []
-    for (c0, c1), v, w, f in zip(wl.chan_groups, wl.vis, wl.weight, wl.flag):
-        groups.append((wg.Grid(N, wl.du, P, c1 - c0, storage=full[c0:c1]),
-                       wg.VisBatch(uvw_d, torch.as_tensor(wl.freq[c0:c1], device=dev), v, w, f), img[c0:c1]))
-    wlst = wg.WorkList(wl.rows * G, G, P)
+    grid = wg.Grid(N, wl.du, P, C, storage=full)
+    c0s = [c0 for c0, _ in wl.chan_groups]
+    freqs = [torch.as_tensor(wl.freq[c0:c1], device=dev) for c0, c1 in wl.chan_groups]
+    batches = [(c0, wg.VisBatch(uvw_d, fq, v, w, f))
+               for (c0, _), fq, v, w, f in zip(wl.chan_groups, freqs, wl.vis, wl.weight, wl.flag)]
     stream = torch.cuda.current_stream()
+    in_bytes = wl.uvw.nbytes + sum(v.numel() * 8 + f.numel() for v, f in zip(wl.vis, wl.flag)) + \
+        wl.weight[0].numel() * 4
 
-    # per group: statistics, the autotuned plan and the gridder's own time under it
-    plans, real, total, t_grid = [], 0, 0, 0.0
-    for g, b, _ in groups:
-        g.zero()
-        wg.vis_compress(g, tab, b, wlst)
-        seg, slots, fixed_r, _ = wg.grid_autotune(g, tab, wlst, candidates=BATCH_PLANS, repeats=1)
-        plans.append((seg, slots, fixed_r))
-        st = wlst.stats()
+    # sizing pass: each group prepared on its own gives the statistics and the number of
+    # gridded entries, so the appended work list is created with room for all of them.  Groups
+    # are split over launches only if the entries of one launch would pass 2^31 - 1.
+    wtmp = wg.WorkList(wl.rows * G, G, P)
+    real, total, counts = 0, 0, []
+    for (c0, c1), (_, b) in zip(wl.chan_groups, batches):
+        view = wg.Grid(N, wl.du, P, c1 - c0, storage=full[c0:c1])
+        wg.vis_compress(view, tab, b, wtmp)
+        st = wtmp.stats()
         real += st["updates"]
         total += st["updates"] + st["updates_saved"]
+        counts.append(st["gridded"])
+    del wtmp, view
+    torch.cuda.empty_cache()
+    launches, cur = [[]], 0
+    for gi, n in enumerate(counts):
+        if cur + n > (1 << 31) - 1 - 1024 and launches[-1]:
+            launches.append([])
+            cur = 0
+        launches[-1].append(gi)
+        cur += n
+    wlst = wg.WorkList(wl.rows * G, G, P, max_entries=max(sum(counts[i] for i in ls) for ls in launches) + 1024)
+
+    def prepare(ls, table):
+        wlst.clear()
+        for gi in ls:
+            c0, b = batches[gi]
+            wg.vis_compress(grid, table, b, wlst, append=True, chan0=c0)
+
+    # the gridder plan, autotuned on the appended batches of the first launch, and the gridder's
+    # own time under it (summed over launches)
+    grid.zero()
+    prepare(launches[0], tab)
+    seg, slots, fixed_r, _ = wg.grid_autotune(grid, tab, wlst, candidates=BATCH_PLANS, repeats=1)
+    plan = (seg, slots, fixed_r)
+    t_grid = 0.0
+    for ls in launches:
+        grid.zero()
+        prepare(ls, tab)
+        wlst.plan(tab, *plan)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        wg.grid_vis(g, tab, wlst)
+        wg.grid_vis(grid, tab, wlst)
         e1.record(stream)
         torch.cuda.synchronize()
         t_grid += e0.elapsed_time(e1)
 
-    cur_plan = [wlst.plan_params]
-
     def step():
-        for (g, b, im), pl in zip(groups, plans):
-            g.zero()
-            if pl != cur_plan[0]:       # re-plan only when the group's plan differs from the last one
-                wlst.plan(tab, *pl)
-                cur_plan[0] = pl
-            wg.vis_compress(g, tab, b, wlst)
-            wg.grid_vis(g, tab, wlst)
-            wg.grid_correct(g, tab, mode=wg.IMAGE_STOKES_I, out=im)
+        grid.zero()
+        for ls in launches:
+            prepare(ls, tab)
+            wg.grid_vis(grid, tab, wlst)        # plans the appended entries, then one gridder launch
+        wg.grid_correct(grid, tab, mode=wg.IMAGE_STOKES_I, out=img)
 
     step()                      # eager once: FFT plans and scratch are allocated outside the capture
     torch.cuda.synchronize()
@@ -715,41 +744,38 @@ def run_batch(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, world, dev)
     value = whole_job_rate(real, ms, world)
+    del graph
 
     # the FP16 table at one polarisation: 4-byte samples halve the sample bytes the gridder
-    # fetches per update (eager, gridder time summed over the groups under the same plans)
+    # fetches per update (eager, the gridder's time under the same plan)
     variants = {}
     if not args.no_variants:
         tab16 = wg.ConvTable.build(wl.du, wl.n_wplanes, wl.w_max, wl.oversample, wl.taper_support,
                                    supports=wl.supports, store="f16")
         t16 = 0.0
-        for (g, b, _), (seg, slots, fixed_r) in zip(groups, plans):
-            g.zero()
-            wlst.plan(tab16, seg, slots, fixed_r)
-            wg.vis_compress(g, tab16, b, wlst)
-            wg.grid_vis(g, tab16, wlst)           # warm-up of this group's launch
-            g.zero()
-            wg.vis_compress(g, tab16, b, wlst)
-            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            v0.record(stream)
-            wg.grid_vis(g, tab16, wlst)
-            v1.record(stream)
-            torch.cuda.synchronize()
+        for ls in launches:
+            for rep in range(2):                 # a warm-up launch, then the timed one
+                grid.zero()
+                prepare(ls, tab16)
+                wlst.plan(tab16, *plan)
+                v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                v0.record(stream)
+                wg.grid_vis(grid, tab16, wlst)
+                v1.record(stream)
+                torch.cuda.synchronize()
             t16 += v0.elapsed_time(v1)
         variants["f16 table"] = {"gridder_ms": round(t16, 3), "real_gridder_G": round(real / (t16 * 1e-3) / 1e9, 3),
                                  "total_gridder_G": round(total / (t16 * 1e-3) / 1e9, 3)}
         del tab16
         torch.cuda.empty_cache()
-        cur_plan[0] = wlst.plan_params
 
-    # end to end through the public API (eager calls): every step copies uvw and each group's
-    # visibilities, weights and flags from pinned host memory and reads each group's Stokes-I
-    # images back.  Groups are double-buffered: group u + 1's inputs copy on a copy stream
-    # while group u computes.
+    # end to end through the public API (eager calls): every step copies uvw and every group's
+    # visibilities, weights and flags from pinned host memory into one set of device buffers
+    # and reads the Stokes-I images back.  The buffers are released once the groups are
+    # prepared, so the next step's copies run on a copy stream while this step's gridder runs;
+    # the images are read back on the copy stream while the next step prepares.
     e2e = None
     if args.e2e_steps > 0:
-        del graph
-        torch.cuda.empty_cache()
         h_uvw = torch.empty(uvw_d.shape, dtype=uvw_d.dtype, pin_memory=True)
         h_uvw.copy_(uvw_d)
         h_vis = [torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for v in wl.vis]
@@ -759,57 +785,56 @@ def run_batch(args, rank, world, local_rank):
             hf.copy_(f)
         h_w = torch.empty(wl.weight[0].shape, dtype=torch.float32, pin_memory=True)
         h_w.copy_(wl.weight[0])
-        h_img = [torch.empty(img[0:G].shape, dtype=img.dtype, pin_memory=True) for _ in range(2)]
-        uvw_s = [torch.empty_like(uvw_d) for _ in range(2)]
-        gslot = [(torch.empty_like(wl.vis[0]), torch.empty_like(wl.weight[0]), torch.empty_like(wl.flag[0]))
-                 for _ in range(2)]
-        freqs = [b.freq for _, b, _ in groups]
+        # the device-resident inputs of the graph-timed steps are released for the copies' buffers
+        del batches
+        wl.vis.clear()
+        wl.flag.clear()
+        torch.cuda.empty_cache()
+        h_img = torch.empty(img.shape, dtype=img.dtype, pin_memory=True)
+        u_d = torch.empty_like(uvw_d)
+        ins = [(torch.empty(hv.shape, dtype=hv.dtype, device=dev), torch.empty(h_w.shape, dtype=h_w.dtype, device=dev),
+                torch.empty(hf.shape, dtype=hf.dtype, device=dev)) for hv, hf in zip(h_vis, h_flag)]
         cstream = torch.cuda.Stream()
-        copied, consumed = [torch.cuda.Event() for _ in range(2)], [torch.cuda.Event() for _ in range(2)]
-        u_copied, u_consumed = [torch.cuda.Event() for _ in range(2)], [torch.cuda.Event() for _ in range(2)]
-        n_groups = len(groups)
+        copied, released, imaged, read = (torch.cuda.Event() for _ in range(4))
         h2d = h_uvw.numel() * 8 + sum(hv.numel() * 8 + hf.numel() + h_w.numel() * 4 for hv, hf in zip(h_vis, h_flag))
         d2h = img.numel() * 4
 
-        def issue(u):
-            k, gi = divmod(u, n_groups)
+        def issue_copies():
             with torch.cuda.stream(cstream):
-                if gi == 0:
-                    cstream.wait_event(u_consumed[k % 2])
-                    uvw_s[k % 2].copy_(h_uvw, non_blocking=True)
-                    u_copied[k % 2].record(cstream)
-                cstream.wait_event(consumed[u % 2])
-                v, w_, f_ = gslot[u % 2]
-                v.copy_(h_vis[gi], non_blocking=True)
-                w_.copy_(h_w, non_blocking=True)
-                f_.copy_(h_flag[gi], non_blocking=True)
-                copied[u % 2].record(cstream)
+                cstream.wait_event(released)
+                u_d.copy_(h_uvw, non_blocking=True)
+                for (v, w_, f_), hv, hf in zip(ins, h_vis, h_flag):
+                    v.copy_(hv, non_blocking=True)
+                    w_.copy_(h_w, non_blocking=True)
+                    f_.copy_(hf, non_blocking=True)
+                copied.record(cstream)
 
         def e2e_steps(n):
-            for ev in consumed + u_consumed:
-                ev.record(stream)
-            issue(0)
-            for u in range(n * n_groups):
-                if u + 1 < n * n_groups:
-                    issue(u + 1)
-                k, gi = divmod(u, n_groups)
-                if gi == 0:
-                    stream.wait_event(u_copied[k % 2])
-                stream.wait_event(copied[u % 2])
-                (g, _, im), (seg, sl, fr) = groups[gi], plans[gi]
-                v, w_, f_ = gslot[u % 2]
-                bt = wg.VisBatch(uvw_s[k % 2], freqs[gi], v, w_, f_)
-                g.zero()
-                if (seg, sl, fr) != cur_plan[0]:
-                    wlst.plan(tab, seg, sl, fr)
-                    cur_plan[0] = (seg, sl, fr)
-                wg.vis_compress(g, tab, bt, wlst)
-                wg.grid_vis(g, tab, wlst)
-                wg.grid_correct(g, tab, mode=wg.IMAGE_STOKES_I, out=im)
-                h_img[u % 2].copy_(im, non_blocking=True)
-                consumed[u % 2].record(stream)
-                if gi == n_groups - 1:
-                    u_consumed[k % 2].record(stream)
+            released.record(stream)
+            read.record(stream)
+            issue_copies()
+            for k in range(n):
+                stream.wait_event(copied)
+                grid.zero()
+                for ls in launches:
+                    wlst.clear()
+                    for gi in ls:
+                        v, w_, f_ = ins[gi]
+                        wg.vis_compress(grid, tab, wg.VisBatch(u_d, freqs[gi], v, w_, f_), wlst, append=True,
+                                        chan0=c0s[gi])
+                    if ls is launches[-1]:
+                        released.record(stream)
+                        if k + 1 < n:
+                            issue_copies()
+                    wg.grid_vis(grid, tab, wlst)
+                stream.wait_event(read)          # the previous step's images have been read back
+                wg.grid_correct(grid, tab, mode=wg.IMAGE_STOKES_I, out=img)
+                imaged.record(stream)
+                with torch.cuda.stream(cstream):
+                    cstream.wait_event(imaged)
+                    h_img.copy_(img, non_blocking=True)
+                    read.record(cstream)
+            stream.wait_event(read)
 
         e2e_steps(1)
         torch.cuda.synchronize()
@@ -823,16 +848,16 @@ def run_batch(args, rank, world, local_rank):
         e2e = {"value": round(whole_job_rate(real, ms_e2e, world), 3), "unit": UNIT,
                "total_rate_G": round(whole_job_rate(total, ms_e2e, world), 3), "ms_per_step": round(ms_e2e, 3),
                "steps": args.e2e_steps, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "pipelining": "channel groups double-buffered on a copy stream; eager calls (no graph)"}
-        del h_uvw, h_vis, h_flag, h_w, h_img, uvw_s, gslot
+               "pipelining": "one set of device input buffers, released after the groups are prepared: the next "
+                             "step's copies run on a copy stream under this step's gridder, and the images are read "
+                             "back on it under the next step's preparation; eager calls (no graph)"}
+        del h_uvw, h_vis, h_flag, h_w, h_img, u_d, ins
         torch.cuda.synchronize()
     peaks, src = _peaks()
     props = torch.cuda.get_device_properties(local_rank)
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = 8.0 * real / (t_grid * 1e-3) / 1e12
-    in_bytes = wl.uvw.nbytes + sum(v.numel() * 8 + f.numel() for v, f in zip(wl.vis, wl.flag)) + \
-        wl.weight[0].numel() * 4
     line = {
         "metric": "gridding/degridding G grid-point updates/s and % roofline at stated grid error",
         "value": round(value, 3),
@@ -846,19 +871,22 @@ def run_batch(args, rank, world, local_rank):
                                               " (slice: %s channels from %d, %s steps)" % (args.n_chan, args.chan0, args.n_times)),
                    "records_per_step": wl.rows * C, "input_bytes": int(in_bytes),
                    "l2": "inputs larger than L2 (no flush needed)", "chan_group": G,
-                   "plans_seg_len_slots_fixed_r": plans, "parallelism": "replicas" if world > 1 else "1 GPU"},
+                   "gridder_launches_per_step": len(launches), "entries_per_launch": [sum(counts[i] for i in ls) for ls in launches],
+                   "plan_seg_len_slots_fixed_r": list(plan), "parallelism": "replicas" if world > 1 else "1 GPU"},
         "rates": {"real_step_G": round(value, 3),
                   "total_step_G": round(whole_job_rate(total, ms, world), 3),
                   "real_gridder_G": round(real / (t_grid * 1e-3) / 1e9, 3),
                   "total_gridder_G": round(total / (t_grid * 1e-3) / 1e9, 3),
                   "gridder_ms": round(t_grid, 3), "updates_real": real, "updates_total": total},
-        "roofline": {"kernel": "k_grid (sum over groups)", "bound": "alu", "achieved": round(achieved, 3),
+        "roofline": {"kernel": "k_grid (one persistent launch over all %d channels)" % C if len(launches) == 1
+                               else "k_grid (sum over %d launches)" % len(launches),
+                     "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
                      "frac": round(achieved / peak_tflops, 4),
                      "peak_source": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flops x %.0f MHz (%s sm_max_mhz)"
                                     % (props.multi_processor_count, sm_mhz, src),
                      "traffic": None},
-        "ceilings": measured_ceilings(real / (t_grid * 1e-3), wl.n_pol),
+        "ceilings": measured_ceilings(real / (t_grid * 1e-3), P),
         "e2e": e2e,
         "variants": variants,
         "gpu_launches": int(captured * args.steps),
@@ -868,7 +896,7 @@ def run_batch(args, rank, world, local_rank):
     if rank == 0 and not args.no_cpu_baseline:
         ot = oracle_table_parallel(wl)
         line["cpu_baseline"] = cpu_sample(args.workload, *CPU_SAMPLE[args.workload], ot=ot)
-        errs = batch_grid_error(dev, plans[-1], ot, stores=("f32",) + (("f16",) if variants else ()))
+        errs = batch_grid_error(dev, plan, ot, stores=("f32",) + (("f16",) if variants else ()))
         line["grid_error"] = errs["f32"]
         if "f16" in errs:
             variants["f16 table"]["grid_error"] = errs["f16"]

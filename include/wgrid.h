@@ -95,6 +95,13 @@ extern "C" {
                              /* onto a one-channel grid (multi-frequency synthesis), and */
                              /* a record compresses into the previous record in that     */
                              /* order; the work list is created with the vis channels    */
+#define WG_PREP_APPEND 32    /* batching (Sec. 5.4: many channels in one gridder launch): */
+                             /* the batch's entries are added after those of the earlier */
+                             /* appended batches (since worklist_clear) and grid onto    */
+                             /* grid channels chan0 .. chan0 + n_chan - 1; its N_p terms */
+                             /* and statistics go into the grid at this call, and one    */
+                             /* grid_vis then grids every appended batch.  Not combined  */
+                             /* with WG_PREP_INTERLEAVE or WG_PREP_WSTACK                */
 
 /* grid_correct modes */
 #define WG_IMAGE_PER_POL 0 /* output float [n_chan][n_pol][N][N]                      */
@@ -233,7 +240,8 @@ typedef struct wg_vis_in {
     const float* weight;    /* device [n_rows][n_chan][n_pol] natural weights (I-3)       */
     const uint8_t* flag;    /* device [n_rows][n_chan][n_pol], 1 = flagged (I-4)          */
     int32_t vis_dtype;      /* WG_VIS_COMPLEX64 (vis is complex64) or WG_VIS_COMPLEX_HALF */
-    int32_t reserved;
+    int32_t chan0;          /* with WG_PREP_APPEND: the grid channel of the batch's first  */
+                            /* channel (chan0 + n_chan <= the grid's channels); else 0     */
     const float* vis_scale; /* device [n_chan] scales for WG_VIS_COMPLEX_HALF, else NULL  */
 } wg_vis_in;
 
@@ -244,6 +252,17 @@ typedef struct wg_worklist wg_worklist;
  * 41 + 16 n_pol bytes per record (placement, entries, weighted visibilities, runs and the
  * degridder's per-entry sums).  Errors: INVALID_ARG, OOM. */
 int worklist_create(int64_t max_records, int32_t n_chan, int32_t n_pol, wg_worklist** out);
+/* As worklist_create, with room for max_entries gridded entries over the batches appended with
+ * WG_PREP_APPEND (Sec. 5.4, batching) and max_records records per batch: 17 bytes per record
+ * (placement and class) plus 24 + 8 n_pol bytes per entry (entry, weighted visibilities, run).
+ * It has no degridding accumulator, so degrid_vis rejects it.  max_entries <= 2^31 - 1.
+ * Entries past max_entries are not written and are counted in wg_stats.dropped.
+ * Errors: INVALID_ARG, OOM. */
+int worklist_create2(int64_t max_records, int64_t max_entries, int32_t n_chan, int32_t n_pol,
+                     wg_worklist** out);
+/* Empties the work list for a new sequence of WG_PREP_APPEND batches (Sec. 5.4, batching):
+ * no entries, statistics zero.  Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
+int worklist_clear(wg_worklist* wl, void* stream);
 /* Frees the work list's device buffers (the preparation outputs of Sec. 4.3.4) and the handle.  NULL is accepted.  Synchronises the
  * device (cudaFree).  Returns WG_OK. */
 int worklist_destroy(wg_worklist* wl);
@@ -307,7 +326,10 @@ int worklist_view(const wg_worklist* wl, const int32_t** entries, const void** g
 
 /* A6: adds every gridded record's gamma_p * C_k[i][j] to grid pixel (y0+i, x0+j) (eq.
  * "gridding"), FP32 accumulation, and adds the batch's normaliser terms and statistics
- * into the grid.  Persistent kernel over the work list's tasks.  Errors: SHAPE, CUDA. */
+ * into the grid.  Persistent kernel over the work list's tasks.  A work list holding
+ * WG_PREP_APPEND batches is gridded in one launch over every appended batch (planned here if
+ * entries were appended since the last plan); their normaliser terms and statistics were
+ * added by vis_compress, and the grid must have the channels they name.  Errors: SHAPE, CUDA. */
 int grid_vis(wg_grid* grid, const wg_table* table, const wg_worklist* wl, void* stream);
 
 /* ---- gridder plan (not in the thesis: GPU work decomposition) ----------------------
@@ -378,8 +400,9 @@ int vis_weight(const wg_grid* grid, const wg_table* table, const wg_vis_in* in, 
  * to every record of the entry's run.
  * After a vis_compress with WG_PREP_CROSS_SWAP, pols 1 and 2 of a psi = -1 record come from
  * grid pols 2 and 1.  Records that are not griddable get 0.  `in` and `wl` must be the batch given to the
- * last vis_compress on `wl`.  vis_out: device complex64 [n_rows][n_chan][n_pol],
- * overwritten.  Errors: INVALID_ARG, SHAPE, CUDA. */
+ * last vis_compress on `wl`, which must not hold WG_PREP_APPEND batches (INVALID_ARG).
+ * vis_out: device complex64 [n_rows][n_chan][n_pol], overwritten.  Errors: INVALID_ARG, SHAPE,
+ * CUDA. */
 int degrid_vis(const wg_grid* grid, const wg_table* table, const wg_vis_in* in,
                const wg_worklist* wl, int32_t mode, void* vis_out, void* stream);
 

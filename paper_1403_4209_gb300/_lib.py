@@ -35,7 +35,7 @@ class TableInfo(ctypes.Structure):
 
 class VisIn(ctypes.Structure):
     _fields_ = [("n_rows", c_i64), ("n_chan", c_i32), ("n_pol", c_i32), ("uvw", c_vp), ("freq_hz", c_vp),
-                ("vis", c_vp), ("weight", c_vp), ("flag", c_vp), ("vis_dtype", c_i32), ("reserved", c_i32),
+                ("vis", c_vp), ("weight", c_vp), ("flag", c_vp), ("vis_dtype", c_i32), ("chan0", c_i32),
                 ("vis_scale", c_vp)]
 
 
@@ -88,6 +88,8 @@ def _load():
         "table_info": (c_i32, [c_vp, P(TableInfo)]),
         "table_copy_to_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
         "worklist_create": (c_i32, [c_i64, c_i32, c_i32, P(c_vp)]),
+        "worklist_create2": (c_i32, [c_i64, c_i64, c_i32, c_i32, P(c_vp)]),
+        "worklist_clear": (c_i32, [c_vp, c_vp]),
         "worklist_destroy": (c_i32, [c_vp]),
         "vis_compress": (c_i32, [c_vp, c_vp, P(VisIn), c_i32, c_vp, c_vp]),
         "worklist_stats": (c_i32, [c_vp, P(Stats), c_vp]),

@@ -26,6 +26,7 @@ IMAGE_STOKES_LINEAR = CONST["WG_IMAGE_STOKES_LINEAR"]
 IMAGE_STOKES_CIRCULAR = CONST["WG_IMAGE_STOKES_CIRCULAR"]
 PREP_CROSS_SWAP = CONST["WG_PREP_CROSS_SWAP"]
 PREP_WSTACK = CONST["WG_PREP_WSTACK"]
+PREP_APPEND = CONST["WG_PREP_APPEND"]
 IMAGE_WSTACK = CONST["WG_IMAGE_WSTACK"]
 PREP_COMPRESS = CONST["WG_PREP_COMPRESS"]
 PREP_UNWEIGHTED = CONST["WG_PREP_UNWEIGHTED"]
@@ -228,13 +229,23 @@ class VisBatch:
 
 
 class WorkList:
-    """Device outputs of the preparation phase for up to max_records records."""
+    """Device outputs of the preparation phase for up to max_records records per batch.
+    max_entries: room for that many gridded entries over the batches appended with
+    vis_compress(..., append=True) (worklist_create2: no degridding accumulator)."""
 
-    def __init__(self, max_records: int, n_chan: int, n_pol: int):
+    def __init__(self, max_records: int, n_chan: int, n_pol: int, max_entries=None):
         h = c_vp()
-        check(lib.worklist_create(int(max_records), int(n_chan), int(n_pol), ctypes.byref(h)), "worklist_create")
+        if max_entries is None:
+            check(lib.worklist_create(int(max_records), int(n_chan), int(n_pol), ctypes.byref(h)), "worklist_create")
+        else:
+            check(lib.worklist_create2(int(max_records), int(max_entries), int(n_chan), int(n_pol), ctypes.byref(h)),
+                  "worklist_create2")
         self._h = h
         self.n_chan, self.n_pol, self.capacity = n_chan, n_pol, max_records
+
+    def clear(self, stream=None):
+        """Empties the work list for a new sequence of appended batches."""
+        check(lib.worklist_clear(self._h, _stream(stream)), "worklist_clear")
 
     @property
     def handle(self):
@@ -280,14 +291,18 @@ class WorkList:
 
 def vis_compress(grid: Grid, table: ConvTable, batch: VisBatch, worklist: WorkList, compress: bool = True,
                  unweighted: bool = False, interleave: bool = False, cross_swap: bool = False, wstack: bool = False,
-                 stream=None):
+                 append: bool = False, chan0: int = 0, stream=None):
     """Preparation phase.  interleave: all channels of the batch grid onto the one-channel
     `grid` in natural record order, compressing across channels (WG_PREP_INTERLEAVE).
     cross_swap: full-Stokes gridding of quad-pol data (WG_PREP_CROSS_SWAP).
-    wstack: w-stacking onto n_chan x K grid channels (WG_PREP_WSTACK, a stacking table)."""
+    wstack: w-stacking onto n_chan x K grid channels (WG_PREP_WSTACK, a stacking table).
+    append: add the batch's entries after the earlier appended ones (WG_PREP_APPEND); the
+    batch grids onto grid channels chan0 .. chan0 + n_chan - 1 and its normaliser terms go
+    into the grid now, and one grid_vis then grids every appended batch."""
     flags = ((PREP_COMPRESS if compress else 0) | (PREP_UNWEIGHTED if unweighted else 0)
              | (PREP_INTERLEAVE if interleave else 0) | (PREP_CROSS_SWAP if cross_swap else 0)
-             | (PREP_WSTACK if wstack else 0))
+             | (PREP_WSTACK if wstack else 0) | (PREP_APPEND if append else 0))
+    batch.struct.chan0 = int(chan0) if append else 0
     check(lib.vis_compress(grid.handle, table.handle, ctypes.byref(batch.struct), flags,
                            worklist.handle, _stream(stream)), "vis_compress")
 

@@ -273,31 +273,37 @@ int worklist_destroy(wg_worklist* h)
     if (!h) return WG_OK;
     WorkList& w = h->w;
     void* ptrs[] = {w.rinfo, w.rclass, w.tile_cnt, w.carry_q, w.carry_last, w.entries, w.gamma, w.runs, w.dacc, w.seg_nblk, w.seg_off,
-                    w.scal, w.chan_base, w.norm_priv, w.norm_batch, w.stat_priv, w.stats, w.task_counter};
+                    w.scal, w.chan_base, w.norm_priv, w.norm_batch, w.stat_priv, w.stats, w.stats_batch, w.task_counter};
     for (void* p : ptrs) cudaFree(p);
     delete h;
     return WG_OK;
 }
 
-int worklist_create(int64_t max_records, int32_t C, int32_t P, wg_worklist** out)
+// a work list for batches of up to max_records records and max_entries gridded entries in all
+// (appended batches); `dacc` adds the degridder's per-entry accumulator
+static int create_worklist(int64_t max_records, int64_t max_entries, int32_t C, int32_t P, bool dacc,
+                           wg_worklist** out)
 {
     t_err[0] = 0;
     if (!out) return fail(WG_E_INVALID_ARG, "worklist_create: null argument");
     *out = nullptr;
     if (max_records < 1 || max_records > ((int64_t)1 << 31) - 1)
         return fail(WG_E_INVALID_ARG, "max_records=%lld must be in [1, 2^31 - 1]", (long long)max_records);
+    if (max_entries < 1 || max_entries > ((int64_t)1 << 31) - 1)
+        return fail(WG_E_INVALID_ARG, "max_entries=%lld must be in [1, 2^31 - 1]", (long long)max_entries);
     if (C < 1 || C > 4096) return fail(WG_E_INVALID_ARG, "n_chan=%d must be in [1, 4096]", C);
     if (P != 1 && P != 2 && P != 4) return fail(WG_E_INVALID_ARG, "n_pol=%d must be 1, 2 or 4", P);
     wg_worklist* h = new (std::nothrow) wg_worklist;
     if (!h) return fail(WG_E_OOM, "host allocation failed");
     WorkList& w = h->w;
     w.cap = max_records;
+    w.ecap = max_entries;
     w.C = C;
     w.P = P;
     const int rpb = std::max(1, kTileRecords / C);
     const int64_t rows_max = (max_records + C - 1) / C;
     w.tile_cap = ((rows_max + rpb - 1) / rpb + 2) * C;
-    w.seg_cap = max_records / kSegLenMin + 2;
+    w.seg_cap = max_entries / kSegLenMin + 2;
     bool ok = true;
     auto al = [&](void** p, size_t bytes) {
         if (ok && dev_malloc(p, bytes) != cudaSuccess) {
@@ -310,10 +316,10 @@ int worklist_create(int64_t max_records, int32_t C, int32_t P, wg_worklist** out
     al((void**)&w.tile_cnt, sizeof(int) * w.tile_cap);
     al((void**)&w.carry_q, sizeof(float2) * w.tile_cap * P);
     al((void**)&w.carry_last, sizeof(int) * w.tile_cap);
-    al((void**)&w.entries, sizeof(int4) * max_records);
-    al((void**)&w.gamma, sizeof(float2) * max_records * P);
-    al((void**)&w.runs, sizeof(int2) * max_records);
-    al((void**)&w.dacc, sizeof(float2) * max_records * P);
+    al((void**)&w.entries, sizeof(int4) * max_entries);
+    al((void**)&w.gamma, sizeof(float2) * max_entries * P);
+    al((void**)&w.runs, sizeof(int2) * max_entries);
+    if (dacc) al((void**)&w.dacc, sizeof(float2) * max_entries * P);
     al((void**)&w.seg_nblk, sizeof(int) * w.seg_cap);
     al((void**)&w.seg_off, sizeof(int) * (w.seg_cap + 1));
     al((void**)&w.scal, sizeof(long long) * 8);
@@ -322,18 +328,45 @@ int worklist_create(int64_t max_records, int32_t C, int32_t P, wg_worklist** out
     al((void**)&w.norm_batch, sizeof(double) * (C * P + 3 * C));
     al((void**)&w.stat_priv, sizeof(unsigned long long) * kNormSlots * ST_N);
     al((void**)&w.stats, sizeof(unsigned long long) * ST_N);
+    al((void**)&w.stats_batch, sizeof(unsigned long long) * ST_N);
     al((void**)&w.task_counter, sizeof(unsigned int) * 4);
     if (!ok) {
         worklist_destroy(h);
-        return fail(WG_E_OOM, "cannot allocate a work list for %lld records", (long long)max_records);
+        return fail(WG_E_OOM, "cannot allocate a work list for %lld records and %lld entries", (long long)max_records,
+                    (long long)max_entries);
     }
     if (cudaMemset(w.scal, 0, sizeof(long long) * 8) != cudaSuccess ||
         cudaMemset(w.stats, 0, sizeof(unsigned long long) * ST_N) != cudaSuccess ||
+        cudaMemset(w.stats_batch, 0, sizeof(unsigned long long) * ST_N) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
         worklist_destroy(h);
         return cuda_fail(cudaGetLastError(), "worklist_create");
     }
     *out = h;
+    return WG_OK;
+}
+
+int worklist_create(int64_t max_records, int32_t C, int32_t P, wg_worklist** out)
+{
+    return create_worklist(max_records, max_records, C, P, true, out);
+}
+
+int worklist_create2(int64_t max_records, int64_t max_entries, int32_t C, int32_t P, wg_worklist** out)
+{
+    return create_worklist(max_records, max_entries, C, P, false, out);
+}
+
+int worklist_clear(wg_worklist* wh, void* stream)
+{
+    t_err[0] = 0;
+    if (!wh) return fail(WG_E_INVALID_ARG, "worklist_clear: null work list");
+    WorkList& w = wh->w;
+    WG_CUDA(cudaMemsetAsync(w.scal, 0, sizeof(long long) * 8, S(stream)));
+    WG_CUDA(cudaMemsetAsync(w.stats, 0, sizeof(unsigned long long) * ST_N, S(stream)));
+    w.append = false;
+    w.chan_hi = 0;
+    w.plan_stale = false;
+    w.N = 0;
     return WG_OK;
 }
 
@@ -368,13 +401,31 @@ int vis_compress(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, int
 {
     t_err[0] = 0;
     if (!gh || !th || !wh) return fail(WG_E_INVALID_ARG, "vis_compress: null handle");
-    int rc = check_vis(gh->g, th->t, in, (flags & WG_PREP_INTERLEAVE) ? 0 : (flags & WG_PREP_WSTACK) ? th->t.K : 1);
-    if (rc != WG_OK) return rc;
     WorkList& w = wh->w;
+    if (flags & WG_PREP_APPEND) {
+        // the batch is a channel slice of the grid: check it against a view of those channels
+        if (flags & (WG_PREP_INTERLEAVE | WG_PREP_WSTACK))
+            return fail(WG_E_INVALID_ARG, "WG_PREP_APPEND is not combined with WG_PREP_INTERLEAVE or WG_PREP_WSTACK");
+        if (!in) return fail(WG_E_INVALID_ARG, "null vis input");
+        if (in->chan0 < 0 || (int64_t)in->chan0 + in->n_chan > gh->g.n_chan)
+            return fail(WG_E_SHAPE, "channels %d..%d of the batch exceed the grid's %d", in->chan0,
+                        in->chan0 + in->n_chan - 1, gh->g.n_chan);
+        if (!w.append && w.N != 0)
+            return fail(WG_E_INVALID_ARG, "the work list holds a batch prepared without WG_PREP_APPEND: call worklist_clear first");
+        Grid slice = gh->g;
+        slice.n_chan = in->n_chan;
+        int rc = check_vis(slice, th->t, in, 1);
+        if (rc != WG_OK) return rc;
+    } else {
+        if (in && in->chan0 != 0) return fail(WG_E_INVALID_ARG, "chan0 is used only with WG_PREP_APPEND");
+        int rc = check_vis(gh->g, th->t, in, (flags & WG_PREP_INTERLEAVE) ? 0 : (flags & WG_PREP_WSTACK) ? th->t.K : 1);
+        if (rc != WG_OK) return rc;
+    }
     if (in->n_chan != w.C || in->n_pol != w.P) return fail(WG_E_SHAPE, "work list was created for %d channels, %d pols", w.C, w.P);
     if (in->n_rows * (int64_t)in->n_chan > w.cap)
         return fail(WG_E_CAPACITY, "%lld records exceed the work list capacity %lld", (long long)(in->n_rows * (int64_t)in->n_chan), (long long)w.cap);
-    if (flags & ~(WG_PREP_COMPRESS | WG_PREP_UNWEIGHTED | WG_PREP_INTERLEAVE | WG_PREP_CROSS_SWAP | WG_PREP_WSTACK))
+    if (flags & ~(WG_PREP_COMPRESS | WG_PREP_UNWEIGHTED | WG_PREP_INTERLEAVE | WG_PREP_CROSS_SWAP | WG_PREP_WSTACK |
+                  WG_PREP_APPEND))
         return fail(WG_E_INVALID_ARG, "unknown vis_compress flags %d", flags);
     if ((flags & WG_PREP_WSTACK) && ((flags & WG_PREP_INTERLEAVE) || !th->t.stacking))
         return fail(WG_E_INVALID_ARG, "WG_PREP_WSTACK needs a WG_TABLE_WSTACK table and no interleaving");
@@ -426,10 +477,18 @@ int grid_vis(wg_grid* gh, const wg_table* th, const wg_worklist* wh, void* strea
     t_err[0] = 0;
     if (!gh || !th || !wh) return fail(WG_E_INVALID_ARG, "grid_vis: null handle");
     Grid& g = gh->g;
-    const WorkList& w = wh->w;
-    if ((w.interleave ? 1 : w.C * w.wstack_k) != g.n_chan || w.P != g.n_pol)
+    WorkList& w = const_cast<WorkList&>(wh->w);      // a stale plan of appended batches is redone
+    if (w.append) {
+        if (w.chan_hi > g.n_chan || w.P != g.n_pol)
+            return fail(WG_E_SHAPE, "appended batches use %d grid channels, the grid has %d", w.chan_hi, g.n_chan);
+    } else if ((w.interleave ? 1 : w.C * w.wstack_k) != g.n_chan || w.P != g.n_pol) {
         return fail(WG_E_SHAPE, "work list shape differs from the grid's");
+    }
     if (w.N != 0 && w.N != g.n) return fail(WG_E_SHAPE, "work list was prepared for N=%d, grid has N=%d", w.N, g.n);
+    if (w.plan_stale) {
+        if (int rc = launch_plan(th->t, w, S(stream))) return rc;
+        w.plan_stale = false;
+    }
     return launch_grid(g, th->t, w, S(stream));
 }
 
@@ -456,6 +515,7 @@ int worklist_plan(wg_worklist* wh, const wg_table* th, const wg_plan* plan, void
     w.slots = plan->slots;
     w.fixed_r = (plan->flags & WG_PLAN_FIXED_R) != 0;
     if (w.N == 0) return WG_OK;     // nothing prepared yet: the next vis_compress uses the plan
+    w.plan_stale = false;
     return launch_plan(th->t, w, S(stream));
 }
 
@@ -553,6 +613,7 @@ int degrid_vis(const wg_grid* gh, const wg_table* th, const wg_vis_in* in, const
     if (!gh || !th || !wh || !vis_out) return fail(WG_E_INVALID_ARG, "degrid_vis: null argument");
     if (mode != WG_DEGRID_PREDICT && mode != WG_DEGRID_ADJOINT) return fail(WG_E_INVALID_ARG, "unknown degrid mode %d", mode);
     const WorkList& w = wh->w;
+    if (w.append) return fail(WG_E_INVALID_ARG, "degrid_vis: the work list holds WG_PREP_APPEND batches");
     int rc = check_vis(gh->g, th->t, in, w.interleave ? 0 : w.wstack_k);
     if (rc != WG_OK) return rc;
     if (w.rows != in->n_rows || w.C != in->n_chan) return fail(WG_E_SHAPE, "work list was prepared for a different batch");

@@ -545,9 +545,20 @@ static int grid_impl(Grid& g, const Table& t, const WorkList& wl, cudaStream_t s
                                                             reinterpret_cast<float4*>(g.err), n4);
         WG_LAUNCHED("k_fold");
     }
+    if (wl.append) return WG_OK;     // appended batches added their N_p terms at vis_compress
     const int n = (g.n_chan / wl.wstack_k) * g.n_pol;     // normaliser rows of the batch
     const int m = std::max(n, (int)ST_N);
     k_accumulate<<<(m + 255) / 256, 256, 0, s>>>(g.norm, wl.norm_batch, n, g.n_pol, wl.wstack_k, g.counters, wl.stats);
+    WG_LAUNCHED("k_accumulate");
+    return WG_OK;
+}
+
+int launch_accumulate(const Grid& g, const WorkList& wl, int chan0, cudaStream_t s)
+{
+    const int n = wl.C * g.n_pol;
+    const int m = std::max(n, (int)ST_N);
+    k_accumulate<<<(m + 255) / 256, 256, 0, s>>>(g.norm + (size_t)chan0 * g.n_pol, wl.norm_batch, n, g.n_pol, 1,
+                                                 g.counters, wl.stats_batch);
     WG_LAUNCHED("k_accumulate");
     return WG_OK;
 }

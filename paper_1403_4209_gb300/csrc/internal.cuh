@@ -94,7 +94,8 @@ struct Table {
 };
 
 struct WorkList {
-    int64_t cap = 0;                      // records
+    int64_t cap = 0;                      // records of one batch
+    int64_t ecap = 0;                     // gridded entries (over the appended batches)
     int C = 0, P = 0;
     int64_t tile_cap = 0;                 // tiles x C counters
     int64_t seg_cap = 0;
@@ -104,6 +105,9 @@ struct WorkList {
     bool interleave = false;              // last batch: channels interleaved onto one grid
     bool cross_swap = false;              // last batch: take-conjugate records swap cross hands
     int wstack_k = 1;                     // last batch: w-stacking planes (1: no stacking)
+    bool append = false;                  // holds batches added with WG_PREP_APPEND
+    int chan_hi = 0;                      // appended batches: one past their highest grid channel
+    bool plan_stale = false;              // entries were appended since the last plan
     // per record (rinfo: placement, written for gridded records and each tile's first row)
     int4* rinfo = nullptr;
     uint8_t* rclass = nullptr;
@@ -125,7 +129,8 @@ struct WorkList {
     double* norm_priv = nullptr;          // [kNormSlots][C][P]
     double* norm_batch = nullptr;         // [C][P]
     unsigned long long* stat_priv = nullptr;  // [kNormSlots][8]
-    unsigned long long* stats = nullptr;  // [8]
+    unsigned long long* stats = nullptr;  // [8] (summed over appended batches)
+    unsigned long long* stats_batch = nullptr;  // [8] the last batch's
     unsigned int* task_counter = nullptr;
     // last batch
     int64_t rows = 0;
@@ -153,11 +158,14 @@ struct PlaceParams {
     int beta_log2;                        // log2(beta), or -1 when beta is not a power of two
     int flag_vec;                         // the flag array is aligned to n_pol bytes
     float kscale_f;                       // (K - 1) / sqrt(w_max): estimate of the nearest plane
+    int chan0;                            // grid channel of the batch's channel 0 (WG_PREP_APPEND)
 };
 
 int launch_prep(const Table& t, const Grid& g, const wg_vis_in& in, int flags, WorkList& wl,
                 cudaStream_t s);
 int launch_grid(Grid& g, const Table& t, const WorkList& wl, cudaStream_t s);
+// adds the last batch's normaliser and statistics into grid channels chan0 .. chan0 + C - 1
+int launch_accumulate(const Grid& g, const WorkList& wl, int chan0, cudaStream_t s);
 int launch_plan(const Table& t, WorkList& wl, cudaStream_t s);
 int launch_weight(const Table& t, const Grid& g, const wg_vis_in& in, int scheme, double robust, int flags,
                   float* out, cudaStream_t s);

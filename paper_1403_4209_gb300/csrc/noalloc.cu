@@ -110,6 +110,7 @@ extern "C" int grid_vis_noalloc(const wg_grid_view* view, const wg_table* th, co
     const int64_t cap = WG_NOALLOC_MAX_RECORDS;
     WorkList w;
     w.cap = cap;
+    w.ecap = cap;
     w.C = C;
     w.P = P;
     const int rpb = std::max(1, kTileRecords / C);
@@ -133,6 +134,7 @@ extern "C" int grid_vis_noalloc(const wg_grid_view* view, const wg_table* th, co
     w.norm_batch = cv.take<double>((int64_t)C * P + 3 * C);
     w.stat_priv = cv.take<unsigned long long>((int64_t)kNormSlots * ST_N);
     w.stats = cv.take<unsigned long long>(ST_N);
+    w.stats_batch = cv.take<unsigned long long>(ST_N);
     w.task_counter = cv.take<unsigned int>(4);
     unsigned long long* counters = cv.take<unsigned long long>(ST_N);
     if (cv.off > kNoallocBytes) return fail(WG_E_CAPACITY, "no-allocation scratch layout exceeds %lld bytes", (long long)kNoallocBytes);

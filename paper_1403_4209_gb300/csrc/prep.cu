@@ -379,12 +379,13 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int* __restrict__ tile_cnt,
 }
 
 __global__ void k_finalize(int* __restrict__ chan_base, int C, const unsigned long long* __restrict__ stat_priv,
-                           unsigned long long* __restrict__ stats, long long* __restrict__ scal, long long cap)
+                           unsigned long long* __restrict__ stats, unsigned long long* __restrict__ stats_batch,
+                           long long* __restrict__ scal, long long cap, int append)
 {
     if (threadIdx.x == 0) {
-        // channel bases and the entry count, held to the work list's capacity (never reached
-        // with consistent counts; a count past it is reported as dropped)
-        long long run = 0;
+        // channel bases and the entry count, held to the work list's capacity (a count past it
+        // is reported as dropped); an appended batch's entries follow those already listed
+        long long run = append ? scal[0] : 0;
         bool over = false;
         for (int c = 0; c < C; ++c) {
             const int t = chan_base[c];
@@ -402,7 +403,8 @@ __global__ void k_finalize(int* __restrict__ chan_base, int C, const unsigned lo
     for (int q = threadIdx.x; q < ST_TASKS; q += blockDim.x) {
         unsigned long long s = 0;
         for (int k = 0; k < kNormSlots; ++k) s += stat_priv[k * ST_N + q];
-        stats[q] = s;
+        stats_batch[q] = s;
+        stats[q] = append ? stats[q] + s : s;
     }
 }
 
@@ -622,7 +624,7 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
             atomicAdd(reinterpret_cast<unsigned long long*>(&scal[3]), 1ull);
             continue;
         }
-        const int ech = pp.wstack ? ch * pp.K + k : gch;   // the grid channel
+        const int ech = pp.wstack ? ch * pp.K + k : gch + pp.chan0;   // the grid channel
         // (-x0) mod S and (-y0) mod S: the residue classes of the footprint's first column and row
         const float inv_s = __frcp_rn((float)S);
         const int rx = mod_small(info.x & 0xFFFF, S, inv_s), ry = mod_small((info.x >> 16) & 0xFFFF, S, inv_s);
@@ -781,6 +783,7 @@ static PlaceParams place_params(const Table& t, int n, double du, int C, int P, 
     pp.zeta_f = t.zeta_f;
     pp.flag_vec = 0;
     pp.kscale_f = (t.K > 1 && t.w_max > 0.0) ? (float)((t.K - 1) / std::sqrt(t.w_max)) : 0.0f;
+    pp.chan0 = 0;
     return pp;
 }
 
@@ -802,11 +805,15 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
     wl.n_tiles = n_tiles;
     wl.N = g.n;
 
+    const bool app = (flags & WG_PREP_APPEND) != 0;
     PlaceParams pp = place_params(t, g.n, g.du, C, P, flags);
     pp.flag_vec = (reinterpret_cast<uintptr_t>(in.flag) % P) == 0;
+    pp.chan0 = app ? in.chan0 : 0;
     wl.interleave = pp.interleave != 0;
     wl.cross_swap = pp.cross_swap != 0;
     wl.wstack_k = pp.wstack ? t.K : 1;
+    wl.chan_hi = app ? std::max(wl.append ? wl.chan_hi : 0, in.chan0 + C) : 0;
+    wl.append = app;
 
     double* lam_inv = reinterpret_cast<double*>(wl.norm_batch + (size_t)C * P);   // [C]
     double* sc = lam_inv + C;                                                     // [C]
@@ -815,8 +822,13 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
 
     WG_CUDA(cudaMemsetAsync(wl.norm_priv, 0, sizeof(double) * kNormSlots * C * P, s));
     WG_CUDA(cudaMemsetAsync(wl.stat_priv, 0, sizeof(unsigned long long) * kNormSlots * ST_N, s));
-    WG_CUDA(cudaMemsetAsync(wl.stats, 0, sizeof(unsigned long long) * ST_N, s));
-    WG_CUDA(cudaMemsetAsync(wl.scal, 0, sizeof(long long) * 4, s));
+    if (app) {
+        // keep the entry count and the dropped count of the earlier batches; the plan is redone
+        WG_CUDA(cudaMemsetAsync(wl.scal + 1, 0, sizeof(long long) * 2, s));
+    } else {
+        WG_CUDA(cudaMemsetAsync(wl.stats, 0, sizeof(unsigned long long) * ST_N, s));
+        WG_CUDA(cudaMemsetAsync(wl.scal, 0, sizeof(long long) * 4, s));
+    }
 
     k_chan_scale<<<(C + 127) / 128, 128, 0, s>>>(in.freq_hz, C, pp.beta_over_du, lam_inv, sc, lam_f, sc_f);
     WG_LAUNCHED("k_chan_scale");
@@ -829,7 +841,7 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
     }
     k_scan_tiles<<<C, 1024, 0, s>>>(wl.tile_cnt, n_tiles, C, wl.chan_base);
     WG_LAUNCHED("k_scan_tiles");
-    k_finalize<<<1, 256, 0, s>>>(wl.chan_base, C, wl.stat_priv, wl.stats, wl.scal, wl.cap);
+    k_finalize<<<1, 256, 0, s>>>(wl.chan_base, C, wl.stat_priv, wl.stats, wl.stats_batch, wl.scal, wl.ecap, app ? 1 : 0);
     WG_LAUNCHED("k_finalize");
     if (rows > 0) {
         const size_t sm = compact_smem(rpb, C, P);
@@ -846,7 +858,7 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
             k_compact<P, VT, IL><<<(unsigned)n_tiles, 512, sm, s>>>(
                 wl.rinfo, wl.rclass, reinterpret_cast<const VT*>(in.vis),
                 std::is_same<VT, float2>::value ? nullptr : in.vis_scale, in.weight, in.flag, rows, rpb,
-                C, wl.tile_cnt, wl.chan_base, pp, wl.entries, wl.gamma, wl.runs, wl.cap, wl.norm_priv, wl.carry_q,
+                C, wl.tile_cnt, wl.chan_base, pp, wl.entries, wl.gamma, wl.runs, wl.ecap, wl.norm_priv, wl.carry_q,
                 wl.carry_last, wl.scal, std::is_same<VT, float2>::value ? vec : 0);
             return WG_OK;
         };
@@ -862,17 +874,24 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
         const int64_t nc = n_tiles * C;
         k_carry<P><<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(wl.carry_q, wl.carry_last, n_tiles, C,
                                                                  pp.interleave ? 1 : C, wl.tile_cnt, wl.chan_base,
-                                                                 wl.gamma, wl.runs, wl.cap, wl.scal);
+                                                                 wl.gamma, wl.runs, wl.ecap, wl.scal);
         WG_LAUNCHED("k_carry");
     }
     k_norm_sum<<<1, 256, 0, s>>>(wl.norm_priv, C * P, wl.norm_batch);
     WG_LAUNCHED("k_norm_sum");
+    if (app) {
+        // the batch's N_p terms and statistics go into its grid channels now; the plan over
+        // every appended batch is made by the next grid_vis (or worklist_plan)
+        wl.plan_stale = true;
+        return launch_accumulate(g, wl, in.chan0, s);
+    }
+    wl.plan_stale = false;
     return launch_plan(t, wl, s);
 }
 
 int launch_plan(const Table& t, WorkList& wl, cudaStream_t s)
 {
-    const int64_t n_seg_max = (wl.cap + wl.seg_len - 1) / wl.seg_len + 1;
+    const int64_t n_seg_max = (wl.ecap + wl.seg_len - 1) / wl.seg_len + 1;
     WG_CUDA(cudaMemsetAsync(wl.seg_nblk, 0, sizeof(int) * std::min<int64_t>(n_seg_max, wl.seg_cap), s));
     k_segments<<<num_sms() * 4, 256, 0, s>>>(wl.entries, wl.scal, t.supports_d, t.K, wl.seg_len, wl.slots,
                                               wl.seg_nblk);
