@@ -42,6 +42,63 @@ __device__ __forceinline__ int mod_small(int a, int S, float inv_s)
     return r;
 }
 
+// ---- untiled bulk copies (TMA) from global into shared memory, completed on an mbarrier ----
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// arrives on the barrier and adds `bytes` to the transfer count its phase waits for
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// bytes (a multiple of 16, both addresses 16-byte aligned) from global to shared memory
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// waits until phase `parity` of the barrier completes, for at most limit_ns; false if it did not
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned long long limit_ns)
+{
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_test(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s: a copy that takes longer is an error
+constexpr unsigned kBulkChunk = 16384;                        // bytes per bulk copy instruction
+constexpr int kCompactThreads = 512;                          // threads of a k_compact block
+
 // some polarisation of record rec unflagged; with `vec` (flag pointer aligned to P bytes) the P
 // flag bytes are read in one load and tested for a zero byte
 __device__ __forceinline__ bool any_unflagged(const uint8_t* __restrict__ flag, int64_t rec, int P, int vec)
@@ -177,7 +234,10 @@ __device__ __forceinline__ Placed place(const double* __restrict__ uvw, int64_t 
                 // the nearest plane in sqrt(w) directly, floor((K-1) sqrt(w / w_max) + 1/2), then
                 // both of its bounds checked with the margin: b_k <= w < b_{k+1} decided, or the
                 // exact steps (an estimate off by one near a bound fails the check)
-                int kk = __float2int_rd(fmaf(pp.kscale_f, sqrtf(wf), 0.5f));
+                // (an estimate only, so the one-instruction approximate square root serves)
+                float sw;
+                asm("sqrt.approx.f32 %0, %1;" : "=f"(sw) : "f"(wf));
+                int kk = __float2int_rd(fmaf(pp.kscale_f, sw, 0.5f));
                 kk = min(max(kk, 0), pp.K - 1);
                 if ((kk == 0 || __ldg(&pp.wbounds_f[kk - 1]) < lo_w) && __ldg(&pp.wbounds_f[kk]) > hi_w)
                     k = kk;
@@ -484,16 +544,130 @@ __device__ __forceinline__ void weighted_vec(const __half2* __restrict__ vis, co
         q[p] = weighted(vis, weight, flag, rec * P + src_pol(p, neg, cross_swap), scale, neg, unweighted, wf[p]);
 }
 
-// One block per tile.  Pass 1 reads the tile's griddable records in natural order (coalesced,
-// vector loads when aligned), keeps eps (1-f) psi-conj(vis) and eps (1-f) per polarisation in
-// shared memory (polarisation-major, conflict-free) and lists the tile's gridded records.
+// the P values and weights of one record from record-major arrays (shared or global memory),
+// with vector loads: qp 8P-byte and wp 4P-byte aligned (P = 1: 8 and 4 bytes)
+template <int P>
+__device__ __forceinline__ void load_rec(const float2* __restrict__ qp, const float* __restrict__ wp, float2 (&q)[P],
+                                         float (&w)[P])
+{
+    if constexpr (P == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(qp);
+        const float4 b = *reinterpret_cast<const float4*>(qp + 2);
+        const float4 c = *reinterpret_cast<const float4*>(wp);
+        q[0] = make_float2(a.x, a.y); q[1] = make_float2(a.z, a.w);
+        q[2] = make_float2(b.x, b.y); q[3] = make_float2(b.z, b.w);
+        w[0] = c.x; w[1] = c.y; w[2] = c.z; w[3] = c.w;
+    } else if constexpr (P == 2) {
+        const float4 a = *reinterpret_cast<const float4*>(qp);
+        const float2 c = *reinterpret_cast<const float2*>(wp);
+        q[0] = make_float2(a.x, a.y); q[1] = make_float2(a.z, a.w);
+        w[0] = c.x; w[1] = c.y;
+    } else {
+        q[0] = qp[0];
+        w[0] = wp[0];
+    }
+}
+
+// loads the P weighted values and weights of record j from the shared staging arrays:
+// polarisation-major [P][cap], or record-major [cap][P] (AOS, the bulk-copied layout)
+template <int P, bool AOS>
+__device__ __forceinline__ void stage_load(const float2* __restrict__ s_q, const float* __restrict__ s_w, int cap, int j,
+                                           float2 (&q)[P], float (&w)[P])
+{
+    if constexpr (AOS) {
+        load_rec<P>(s_q + (size_t)j * P, s_w + (size_t)j * P, q, w);
+    } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            q[p] = s_q[(size_t)p * cap + j];
+            w[p] = s_w[(size_t)p * cap + j];
+        }
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void stage_store_aos(float2* __restrict__ s_q, float* __restrict__ s_w, int j,
+                                                const float2 (&q)[P], const float (&w)[P])
+{
+    if constexpr (P == 4) {
+        *reinterpret_cast<float4*>(s_q + j * 4) = make_float4(q[0].x, q[0].y, q[1].x, q[1].y);
+        *reinterpret_cast<float4*>(s_q + j * 4 + 2) = make_float4(q[2].x, q[2].y, q[3].x, q[3].y);
+        *reinterpret_cast<float4*>(s_w + j * 4) = make_float4(w[0], w[1], w[2], w[3]);
+    } else if constexpr (P == 2) {
+        *reinterpret_cast<float4*>(s_q + j * 2) = make_float4(q[0].x, q[0].y, q[1].x, q[1].y);
+        *reinterpret_cast<float2*>(s_w + j * 2) = make_float2(w[0], w[1]);
+    } else {
+        s_q[j] = q[0];
+        s_w[j] = w[0];
+    }
+}
+
+// the P flag bytes of record rec in one load (flag pointer aligned to P bytes)
+template <int P>
+__device__ __forceinline__ unsigned flags_of(const uint8_t* __restrict__ flag, int64_t rec)
+{
+    if constexpr (P == 4) return __ldg(reinterpret_cast<const unsigned*>(flag) + rec);
+    else if constexpr (P == 2) return __ldg(reinterpret_cast<const unsigned short*>(flag) + rec);
+    else return __ldg(flag + rec);
+}
+
+// Writes one run of a channel sequence (or of the interleaved sequence): for a head, its entry,
+// gamma and run (first and last row, or record when interleaved); for the compressed records a
+// tile starts with (a carry: the end of a run begun in an earlier tile), their sum in
+// carry[tile][sequence] for k_carry.  Adds zeta(sub-kernel) x sum eps (1-f) to the normaliser.
+template <int P>
+__device__ __forceinline__ void emit_run(const int4& info, bool is_carry, int64_t tile, int C, int ch, int gch,
+                                         int64_t first, int64_t last, const float2 (&acc)[P], const float (&wsum)[P],
+                                         const PlaceParams& pp, float* s_norm, const int* __restrict__ tile_off,
+                                         const int* __restrict__ chan_base, int4* __restrict__ entries,
+                                         float2* __restrict__ gamma, int2* __restrict__ runs, int64_t cap_entries,
+                                         float2* __restrict__ carry_q, int* __restrict__ carry_last,
+                                         long long* __restrict__ scal)
+{
+    const int k = info.w & 0xFFF;
+    const int S = __ldg(&pp.supports[k]);
+    const int sub = (info.z - __ldg(&pp.offsets[k])) / (S * S);
+    const float zeta = __ldg(&pp.zeta_f[k * pp.beta * pp.beta + sub]);
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+        if (wsum[p] != 0.f) atomicAdd(&s_norm[gch * P + p], zeta * wsum[p]);
+    if (is_carry) {
+        const int64_t c = tile * C + gch;
+#pragma unroll
+        for (int p = 0; p < P; ++p) carry_q[c * P + p] = acc[p];
+        carry_last[c] = (int)last;
+        return;
+    }
+    const int rank = (info.w >> 16) & 0xFFFF;
+    const int dst = chan_base[gch] + tile_off[tile * C + gch] + rank;
+    if (dst < 0 || (int64_t)dst >= cap_entries) {   // cannot happen with a consistent scan
+        atomicAdd(reinterpret_cast<unsigned long long*>(&scal[3]), 1ull);
+        return;
+    }
+    const int ech = pp.wstack ? ch * pp.K + k : gch + pp.chan0;   // the grid channel
+    // (-x0) mod S and (-y0) mod S: the residue classes of the footprint's first column and row
+    const float inv_s = __frcp_rn((float)S);
+    const int rx = mod_small(info.x & 0xFFFF, S, inv_s), ry = mod_small((info.x >> 16) & 0xFFFF, S, inv_s);
+    const int cuv = (rx ? S - rx : 0) | ((ry ? S - ry : 0) << 16);
+    entries[dst] = make_int4(info.x, cuv, info.z, k | (ech << 16));
+#pragma unroll
+    for (int p = 0; p < P; ++p) gamma[(int64_t)dst * P + p] = acc[p];
+    runs[dst] = make_int2((int)first, (int)last);
+}
+
+// One block per tile.  Pass 1 stages the tile's records in shared memory: eps (1-f)
+// psi-conj(vis) and eps (1-f) per polarisation, and lists the tile's gridded records.  With
+// BULK (FP32 visibilities, 16-byte aligned tiles) the tile's visibilities and weights arrive
+// by bulk asynchronous copies (TMA) into record-major staging arrays, issued before anything
+// else, while the threads read the class bytes and flags; each thread then weighs its records
+// in place.  Otherwise every record is read with vector loads into polarisation-major arrays.
 // Pass 2: each listed record sums its run of compressed successors (same channel, following
 // rows) from shared memory in row order, continuing into the following tiles through global
 // memory when the run crosses the tile's end; it writes its entry, gamma and run, and adds
 // zeta(sub-kernel) x sum eps (1-f) to the normaliser (all records of a run share the
 // sub-kernel).
-template <int P, typename VT, bool IL>
-__global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo, const uint8_t* __restrict__ rclass,
+template <int P, typename VT, bool IL, bool BULK>
+__global__ void __launch_bounds__(kCompactThreads, 2) k_compact(const int4* __restrict__ rinfo, const uint8_t* __restrict__ rclass,
                                                  const VT* __restrict__ vis, const float* __restrict__ vis_scale,
                                                  const float* __restrict__ weight, const uint8_t* __restrict__ flag,
                                                  int64_t rows, int rpb, int C, const int* __restrict__ tile_off,
@@ -503,59 +677,158 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
                                                  double* __restrict__ norm_priv, float2* __restrict__ carry_q,
                                                  int* __restrict__ carry_last, long long* __restrict__ scal, int vec)
 {
+    static_assert(!BULK || std::is_same<VT, float2>::value, "bulk staging takes FP32 visibilities");
     extern __shared__ __align__(16) unsigned char smem[];
     const int64_t tile = blockIdx.x;
     const int64_t row0 = tile * rpb;
     const int nrows = (int)min((int64_t)rpb, rows - row0);
     const int nrec = nrows * C;
     const int cap = rpb * C;
-    float2* s_q = reinterpret_cast<float2*>(smem);                        // [P][cap]
-    float* s_w = reinterpret_cast<float*>(s_q + (size_t)cap * P);         // [P][cap]
+    float2* s_q = reinterpret_cast<float2*>(smem);                        // [P][cap] or [cap][P]
+    float* s_w = reinterpret_cast<float*>(s_q + (size_t)cap * P);         // [P][cap] or [cap][P]
     float* s_norm = s_w + (size_t)cap * P;                                // [C][P]
     int* s_heads = reinterpret_cast<int*>(s_norm + (size_t)C * P);        // [cap]
     uint8_t* s_cls = reinterpret_cast<uint8_t*>(s_heads + cap);           // [cap]
     __shared__ int n_heads;
+    __shared__ int s_abort;
+    __shared__ unsigned long long s_bar;
     const int unweighted = pp.unweighted;
 
-    if (threadIdx.x == 0) n_heads = 0;
+    // the bulk copies cover whole 16-byte units of the tile's visibilities and weights; a
+    // ragged last tile reads its remaining records directly
+    const unsigned bytes_v = BULK ? ((unsigned)nrec * P * 8u) & ~15u : 0u;
+    const unsigned bytes_w = BULK ? ((unsigned)nrec * P * 4u) & ~15u : 0u;
+    if constexpr (BULK) {
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0) {
+                mbar_init(&s_bar, 1);
+                mbar_arrive_expect(&s_bar, bytes_v + bytes_w);
+            }
+            __syncwarp();
+            const unsigned nv = (bytes_v + kBulkChunk - 1) / kBulkChunk, nw = (bytes_w + kBulkChunk - 1) / kBulkChunk;
+            const char* gv = reinterpret_cast<const char*>(vis + row0 * C * P);
+            const char* gw = reinterpret_cast<const char*>(weight + row0 * C * P);
+            for (unsigned i = threadIdx.x; i < nv + nw; i += 32) {
+                const bool isv = i < nv;
+                const unsigned off = (isv ? i : i - nv) * kBulkChunk;
+                const unsigned tot = isv ? bytes_v : bytes_w;
+                bulk_to_smem(reinterpret_cast<char*>(isv ? (void*)s_q : (void*)s_w) + off, (isv ? gv : gw) + off,
+                             min(kBulkChunk, tot - off), &s_bar);
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        n_heads = 0;
+        s_abort = 0;
+    }
     for (int i = threadIdx.x; i < C * P; i += blockDim.x) s_norm[i] = 0.f;
     __syncthreads();
-    for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
-        const int64_t rec = row0 * C + j;
-        const int cls = rclass[rec];
-        s_cls[j] = (uint8_t)cls;
-        if (!(cls & 4)) continue;                       // not griddable
-        if (cls & 1) s_heads[atomicAdd(&n_heads, 1)] = j;
-        const float scale = vis_scale ? vis_scale[j % C] : 1.0f;
-        const bool neg = (cls >> 3) & 1;
-        if (vec) {
-            float2 q[P];
-            float wf[P];
-            weighted_vec<P>(vis, weight, flag, rec, scale, neg, unweighted, pp.cross_swap, q, wf);
+    if constexpr (BULK) {
+        constexpr int kU = 4;                    // records per thread whose class and flag loads are issued together
+        bool waited = false, ok = true;
+        for (int j0 = threadIdx.x; j0 < nrec; j0 += kU * blockDim.x) {
+            int cls[kU];
+            unsigned fl[kU];
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                s_q[(size_t)p * cap + j] = q[p];
-                s_w[(size_t)p * cap + j] = wf[p];
+            for (int u = 0; u < kU; ++u) {
+                const int j = j0 + u * (int)blockDim.x;
+                cls[u] = 0;
+                fl[u] = 0u;
+                if (j < nrec) {
+                    const int64_t rec = row0 * C + j;
+                    cls[u] = rclass[rec];
+                    fl[u] = flags_of<P>(flag, rec);
+                }
             }
-        } else {
+            if (!waited) {
+                waited = true;
+                ok = mbar_wait(&s_bar, 0, kWaitLimitNs);
+                if (!ok) s_abort = 1;
+            }
+            if (!ok) continue;
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                float wf;
-                s_q[(size_t)p * cap + j] = weighted(vis, weight, flag, rec * P + src_pol(p, neg, pp.cross_swap), scale,
-                                                    neg, unweighted, wf);
-                s_w[(size_t)p * cap + j] = wf;
+            for (int u = 0; u < kU; ++u) {
+                const int j = j0 + u * (int)blockDim.x;
+                if (j >= nrec) continue;
+                const int c = cls[u];
+                s_cls[j] = (uint8_t)c;
+                if (!(c & 4)) continue;                  // not griddable
+                if (c & 1) s_heads[atomicAdd(&n_heads, 1)] = j;
+                const int64_t rec = row0 * C + j;
+                float2 v[P];
+                float w[P];
+                if ((unsigned)(j + 1) * P * 8u <= bytes_v && (unsigned)(j + 1) * P * 4u <= bytes_w)
+                    stage_load<P, true>(s_q, s_w, cap, j, v, w);
+                else                                             // the ragged end of the last tile
+                    load_rec<P>(vis + rec * P, weight + rec * P, v, w);
+                const bool neg = (c >> 3) & 1;
+                unsigned f = fl[u];
+                if constexpr (P == 4) {
+                    // cross-hand swap (src_pol) with static indices: pol 1 takes pol 2's input and back
+                    if (pp.cross_swap && neg) {
+                        const float2 tv = v[1];
+                        v[1] = v[2];
+                        v[2] = tv;
+                        const float tw = w[1];
+                        w[1] = w[2];
+                        w[2] = tw;
+                        f = (f & 0xFF0000FFu) | ((f >> 8) & 0x0000FF00u) | ((f << 8) & 0x00FF0000u);
+                    }
+                }
+                float2 q[P];
+                float wf[P];
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    wf[p] = unweighted ? 1.0f : w[p] * (1.0f - (float)((f >> (8 * p)) & 0xFFu));
+                    q[p] = make_float2(wf[p] * v[p].x, (neg ? -1.f : 1.f) * (wf[p] * v[p].y));
+                }
+                stage_store_aos<P>(s_q, s_w, j, q, wf);
+            }
+        }
+    } else {
+        for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
+            const int64_t rec = row0 * C + j;
+            const int cls = rclass[rec];
+            s_cls[j] = (uint8_t)cls;
+            if (!(cls & 4)) continue;                       // not griddable
+            if (cls & 1) s_heads[atomicAdd(&n_heads, 1)] = j;
+            const float scale = vis_scale ? vis_scale[j % C] : 1.0f;
+            const bool neg = (cls >> 3) & 1;
+            if (vec) {
+                float2 q[P];
+                float wf[P];
+                weighted_vec<P>(vis, weight, flag, rec, scale, neg, unweighted, pp.cross_swap, q, wf);
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    s_q[(size_t)p * cap + j] = q[p];
+                    s_w[(size_t)p * cap + j] = wf[p];
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    float wf;
+                    s_q[(size_t)p * cap + j] = weighted(vis, weight, flag, rec * P + src_pol(p, neg, pp.cross_swap),
+                                                        scale, neg, unweighted, wf);
+                    s_w[(size_t)p * cap + j] = wf;
+                }
             }
         }
     }
     __syncthreads();
+    if (BULK && s_abort) {                 // a bulk copy did not complete in time: nothing of the tile is written
+        if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&scal[3]), 1ull);
+        for (int i = threadIdx.x; i < C; i += blockDim.x) carry_last[tile * C + i] = -1;
+        mbar_wait(&s_bar, 0, kWaitLimitNs);       // copies still in flight land before the block exits
+        return;
+    }
 
     // pass 2: work items are the tile's gridded records (runs summed inside the tile) and, per
     // sequence (channel; the one natural-order sequence when interleaved), the compressed
     // records the tile starts with, which continue a run of an earlier tile: their sum is left
-    // in carry[tile][sequence] for k_carry to add to that run's entry.
+    // in carry[tile][sequence] for k_carry to add to that run's entry.  A run is walked with the
+    // next record's class and values loaded together (one shared-memory latency per record).
     const int nh = n_heads;
     const int n_seq = IL ? 1 : C;
-    const int stride = IL ? 1 : C;
     for (int h = threadIdx.x; h < nh + n_seq; h += blockDim.x) {
         const bool is_carry = h >= nh;
         const int j = is_carry ? h - nh : s_heads[h];          // a carry starts at the sequence's first record
@@ -569,71 +842,34 @@ __global__ void __launch_bounds__(512) k_compact(const int4* __restrict__ rinfo,
         const int4 info = rinfo[rec];
         float2 acc[P];
         float wsum[P];
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            acc[p] = s_q[(size_t)p * cap + j];
-            wsum[p] = s_w[(size_t)p * cap + j];
-        }
+        stage_load<P, BULK>(s_q, s_w, cap, j, acc, wsum);
         // the run inside the tile: successors (next rows of the channel, or next records when
         // interleaved) while compressed; `last` is its last row (interleaved: record)
-        int64_t last = IL ? rec : row;
-        if constexpr (!IL) {
-            for (int r2 = rr + 1; r2 < nrows; ++r2) {
-                const int j2 = r2 * C + ch;
-                if (!(s_cls[j2] & 2)) break;
+        const int step = IL ? 1 : C;
+        const int jend = IL ? nrec : nrows * C;
+        int j2 = j + step, jl = j;
+        if (j2 < jend) {
+            int c2 = s_cls[j2];
+            float2 q[P];
+            float w[P];
+            stage_load<P, BULK>(s_q, s_w, cap, j2, q, w);
+            while (c2 & 2) {
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    const float2 q = s_q[(size_t)p * cap + j2];
-                    acc[p].x += q.x;
-                    acc[p].y += q.y;
-                    wsum[p] += s_w[(size_t)p * cap + j2];
+                    acc[p].x += q[p].x;
+                    acc[p].y += q[p].y;
+                    wsum[p] += w[p];
                 }
-                last = row0 + r2;
-            }
-        } else {
-            for (int j2 = j + 1; j2 < nrec; ++j2) {
-                if (!(s_cls[j2] & 2)) break;
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const float2 q = s_q[(size_t)p * cap + j2];
-                    acc[p].x += q.x;
-                    acc[p].y += q.y;
-                    wsum[p] += s_w[(size_t)p * cap + j2];
-                }
-                last = row0 * C + j2;
+                jl = j2;
+                j2 += step;
+                if (j2 >= jend) break;
+                c2 = s_cls[j2];
+                stage_load<P, BULK>(s_q, s_w, cap, j2, q, w);
             }
         }
-        (void)stride;
-        const int k = info.w & 0xFFF;
-        const int S = __ldg(&pp.supports[k]);
-        const int sub = (info.z - __ldg(&pp.offsets[k])) / (S * S);
-        const float zeta = __ldg(&pp.zeta_f[k * pp.beta * pp.beta + sub]);
-#pragma unroll
-        for (int p = 0; p < P; ++p)
-            if (wsum[p] != 0.f) atomicAdd(&s_norm[gch * P + p], zeta * wsum[p]);
-        if (is_carry) {
-            const int64_t c = tile * C + gch;
-#pragma unroll
-            for (int p = 0; p < P; ++p) carry_q[c * P + p] = acc[p];
-            carry_last[c] = (int)last;
-            continue;
-        }
-        const int rank = (info.w >> 16) & 0xFFFF;
-        const int dst = chan_base[gch] + tile_off[tile * C + gch] + rank;
-        if (dst < 0 || (int64_t)dst >= cap_entries) {   // cannot happen with a consistent scan
-            atomicAdd(reinterpret_cast<unsigned long long*>(&scal[3]), 1ull);
-            continue;
-        }
-        const int ech = pp.wstack ? ch * pp.K + k : gch + pp.chan0;   // the grid channel
-        // (-x0) mod S and (-y0) mod S: the residue classes of the footprint's first column and row
-        const float inv_s = __frcp_rn((float)S);
-        const int rx = mod_small(info.x & 0xFFFF, S, inv_s), ry = mod_small((info.x >> 16) & 0xFFFF, S, inv_s);
-        const int cuv = (rx ? S - rx : 0) | ((ry ? S - ry : 0) << 16);
-        entries[dst] = make_int4(info.x, cuv, info.z, k | (ech << 16));
-#pragma unroll
-        for (int p = 0; p < P; ++p) gamma[(int64_t)dst * P + p] = acc[p];
-        // runs: first and last row of the channel, or first and last record when interleaved
-        runs[dst] = make_int2(IL ? (int)rec : (int)row, (int)last);
+        const int64_t last = IL ? row0 * C + jl : row0 + jl / C;
+        emit_run<P>(info, is_carry, tile, C, ch, gch, IL ? rec : row, last, acc, wsum, pp, s_norm, tile_off, chan_base,
+                    entries, gamma, runs, cap_entries, carry_q, carry_last, scal);
     }
     __syncthreads();
     const int slot = (int)(tile % kNormSlots);
@@ -850,12 +1086,17 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
         const int vec = (va % 16 == 0) && (wa % (4 * P) == 0) && (fa % P == 0);
         if (sm > 227 * 1024)
             return fail(WG_E_CAPACITY, "%d channels x %d polarisations do not fit one preparation tile", C, P);
-        auto launch = [&](auto vt, auto il) -> int {
+        // bulk staging: FP32 visibilities and weights whose every tile starts on a 16-byte boundary
+        const bool bulk = in.vis_dtype == WG_VIS_COMPLEX64 && vec && va % 16 == 0 && wa % 16 == 0 &&
+                          ((int64_t)rpb * C * P) % 4 == 0;
+        auto launch = [&](auto vt, auto il, auto bk) -> int {
             using VT = decltype(vt);
             constexpr bool IL = decltype(il)::value;
+            constexpr bool BULK = decltype(bk)::value;
             if (sm > 48 * 1024)
-                WG_CUDA(cudaFuncSetAttribute(k_compact<P, VT, IL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            k_compact<P, VT, IL><<<(unsigned)n_tiles, 512, sm, s>>>(
+                WG_CUDA(cudaFuncSetAttribute(k_compact<P, VT, IL, BULK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sm));
+            k_compact<P, VT, IL, BULK><<<(unsigned)n_tiles, kCompactThreads, sm, s>>>(
                 wl.rinfo, wl.rclass, reinterpret_cast<const VT*>(in.vis),
                 std::is_same<VT, float2>::value ? nullptr : in.vis_scale, in.weight, in.flag, rows, rpb,
                 C, wl.tile_cnt, wl.chan_base, pp, wl.entries, wl.gamma, wl.runs, wl.ecap, wl.norm_priv, wl.carry_q,
@@ -863,10 +1104,14 @@ static int prep_impl(const Table& t, const Grid& g, const wg_vis_in& in, int fla
             return WG_OK;
         };
         int rc;
+        using T = std::true_type;
+        using F = std::false_type;
         if (in.vis_dtype == WG_VIS_COMPLEX_HALF)
-            rc = pp.interleave ? launch(__half2{}, std::true_type{}) : launch(__half2{}, std::false_type{});
+            rc = pp.interleave ? launch(__half2{}, T{}, F{}) : launch(__half2{}, F{}, F{});
+        else if (bulk)
+            rc = pp.interleave ? launch(float2{}, T{}, T{}) : launch(float2{}, F{}, T{});
         else
-            rc = pp.interleave ? launch(float2{}, std::true_type{}) : launch(float2{}, std::false_type{});
+            rc = pp.interleave ? launch(float2{}, T{}, F{}) : launch(float2{}, F{}, F{});
         if (rc != WG_OK) return rc;
         WG_LAUNCHED("k_compact");
     }
