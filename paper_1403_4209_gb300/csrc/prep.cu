@@ -101,7 +101,8 @@ constexpr int kCompactThreads = 512;                          // threads of a k_
 
 // some polarisation of record rec unflagged; with `vec` (flag pointer aligned to P bytes) the P
 // flag bytes are read in one load and tested for a zero byte
-__device__ __forceinline__ bool any_unflagged(const uint8_t* __restrict__ flag, int64_t rec, int P, int vec)
+template <typename IDX>
+__device__ __forceinline__ bool any_unflagged(const uint8_t* __restrict__ flag, IDX rec, int P, int vec)
 {
     if (vec && P == 4) {
         const unsigned w = __ldg(reinterpret_cast<const unsigned*>(flag) + rec);
@@ -207,9 +208,13 @@ __device__ __forceinline__ bool place_exact(const double* __restrict__ uvw, int6
 // Placement of one record.  The cell (q_u, q_v) and the plane k are decided from float
 // estimates when the estimate's error bound cannot cross a rounding or plane boundary, which
 // gives the same decisions as the FP64 steps (place_exact) that every other record takes.
-__device__ __forceinline__ Placed place(const double* __restrict__ uvw, int64_t row, const RowF& rf, double lam_inv,
-                                        double sc, float lam_f, float sc_f, const uint8_t* __restrict__ flag,
-                                        int64_t rec, int P, const PlaceParams& pp)
+// (lam_inv and sc are the channels' FP64 scales, read only by the exact steps; rec indexes the
+// flags from `flag`, a 32-bit record index within a tile or a 64-bit one)
+template <typename IDX>
+__device__ __forceinline__ Placed place(const double* __restrict__ uvw, int64_t row, const RowF& rf,
+                                        const double* __restrict__ lam_inv, const double* __restrict__ sc, int ch,
+                                        float lam_f, float sc_f, const uint8_t* __restrict__ flag, IDX rec, int P,
+                                        const PlaceParams& pp)
 {
     Placed o;
     o.info = make_int4(0, 0, 0, rf.neg ? (1 << kBitNeg) : 0);
@@ -246,7 +251,7 @@ __device__ __forceinline__ Placed place(const double* __restrict__ uvw, int64_t 
             }
         }
     }
-    if (!fast && !place_exact(uvw, row, lam_inv, sc, rf.neg, pp, iqu, iqv, k)) return o;
+    if (!fast && !place_exact(uvw, row, lam_inv[ch], sc[ch], rf.neg, pp, iqu, iqv, k)) return o;
     if (iqu >= pp.qlim || iqu <= -pp.qlim || iqv >= pp.qlim || iqv <= -pp.qlim) return o;   // off the grid
     const int b = pp.beta;
     const int xc = floor_div32(2 * iqu + b - 1, 2 * b, pp.beta_log2 + 1);
@@ -258,7 +263,8 @@ __device__ __forceinline__ Placed place(const double* __restrict__ uvw, int64_t 
     if (x0 < 0 || y0 < 0 || x0 + S - 1 > pp.N - 1 || y0 + S - 1 > pp.N - 1) return o;
     if (!unflagged) return o;
     const int sub = (fv - pp.lo) * pp.beta + (fu - pp.lo);
-    o.info.x = x0 | (y0 << 16);        // info.y (the footprint's residues) is filled for entries only
+    o.info.x = x0 | (y0 << 16);
+    o.info.y = S;                      // the support, for the statistics (entries take the footprint's residues here)
     o.info.z = __ldg(&pp.offsets[k]) + sub * S * S;
     o.info.w |= k | (1 << kBitGd);
     o.S = S;
@@ -316,50 +322,69 @@ __global__ void __launch_bounds__(512, 3) k_classify(const double* __restrict__ 
         if (row0 + rr >= 0) s_row[rr + 1] = row_f(uvw, row0 + rr);
     __syncthreads();
 
+    // the records of this thread are j = threadIdx.x + i blockDim.x; their (row in the tile,
+    // channel) pairs are stepped from one to the next, and global arrays are indexed from the
+    // tile's first record with 32-bit offsets
+    const int2 q0 = divmod_small(threadIdx.x, C, inv_c);
+    const int2 dq = divmod_small(blockDim.x, C, inv_c);
+    const uint8_t* flag_t = flag + row0 * C * P;
+
     // pass 1: placement
-    for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
-        const int2 qr = divmod_small(j, C, inv_c);
-        const int rr = qr.x, ch = qr.y;
-        const int64_t row = row0 + rr, rec = row * C + ch;
-        s_info[j] = place(uvw, row, s_row[rr + 1], lam_inv[ch], sc[ch], lam_f[ch], sc_f[ch], flag, rec, P, pp).info;
+    {
+        int rr = q0.x, ch = q0.y;
+        for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
+            s_info[j] = place(uvw, row0 + rr, s_row[rr + 1], lam_inv, sc, ch, lam_f[ch], sc_f[ch], flag_t, j, P, pp).info;
+            rr += dq.x;
+            ch += dq.y;
+            if (ch >= C) {
+                ch -= C;
+                ++rr;
+            }
+        }
     }
     __syncthreads();
 
     // pass 2: compression indicator, g, statistics
     // per thread at most cap / blockDim records, so the counts fit 32 bits, and so do warp sums
     unsigned n_gd = 0, n_g = 0, n_c = 0, u_g = 0, u_c = 0;
-    for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
-        const int2 qr = divmod_small(j, C, inv_c);
-        const int rr = qr.x, ch = qr.y;
-        const int64_t row = row0 + rr, rec = row * C + ch;
-        const int4 info = s_info[j];
-        const int gd = (info.w >> kBitGd) & 1;
-        int c = 0;
-        // the predecessor: the previous row of the channel, or with interleaving the previous
-        // record in natural order (the last channel of the previous row for channel 0)
-        if (pp.compress && gd && (pp.interleave ? rec > 0 : row > 0)) {
-            int4 pinfo;
-            if (!pp.interleave && rr > 0) {
-                pinfo = s_info[j - C];
-            } else if (pp.interleave && j > 0) {
-                pinfo = s_info[j - 1];
-            } else {
-                const int pc = pp.interleave ? C - 1 : ch;
-                pinfo = place(uvw, row - 1, s_row[0], lam_inv[pc], sc[pc], lam_f[pc], sc_f[pc], flag,
-                              (row - 1) * C + pc, P, pp).info;
+    {
+        int rr = q0.x, ch = q0.y;
+        for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
+            const int4 info = s_info[j];
+            const int gd = (info.w >> kBitGd) & 1;
+            int c = 0;
+            // the predecessor: the previous row of the channel, or with interleaving the previous
+            // record in natural order (the last channel of the previous row for channel 0)
+            if (pp.compress && gd && (row0 + rr > 0 || (pp.interleave && j > 0))) {
+                int4 pinfo;
+                if (!pp.interleave && rr > 0) {
+                    pinfo = s_info[j - C];
+                } else if (pp.interleave && j > 0) {
+                    pinfo = s_info[j - 1];
+                } else {                          // the first row of the tile: the row before it
+                    const int pc = pp.interleave ? C - 1 : ch;
+                    pinfo = place(uvw, row0 - 1, s_row[0], lam_inv, sc, pc, lam_f[pc], sc_f[pc], flag_t, pc - C, P,
+                                  pp).info;
+                }
+                c = ((pinfo.w >> kBitGd) & 1) && pinfo.x == info.x && pinfo.z == info.z;
             }
-            c = ((pinfo.w >> kBitGd) & 1) && pinfo.x == info.x && pinfo.z == info.z;
-        }
-        const int g = gd & (c ^ 1);
-        s_gc[j] = (unsigned char)(g | (c << 1) | (gd << 2) | (((info.w >> kBitNeg) & 1) << 3));
-        s_scan[pp.interleave ? j : ch * nrows + rr] = g;
-        if (gd) {
-            const unsigned S = (unsigned)__ldg(&pp.supports[info.w & 0xFFF]);
-            n_gd += 1;
-            n_g += g;
-            n_c += c;
-            u_g += g ? S * S : 0u;
-            u_c += c ? S * S : 0u;
+            const int g = gd & (c ^ 1);
+            s_gc[j] = (unsigned char)(g | (c << 1) | (gd << 2) | (((info.w >> kBitNeg) & 1) << 3));
+            s_scan[pp.interleave ? j : ch * nrows + rr] = g;
+            if (gd) {
+                const unsigned S = (unsigned)info.y;
+                n_gd += 1;
+                n_g += g;
+                n_c += c;
+                u_g += g ? S * S : 0u;
+                u_c += c ? S * S : 0u;
+            }
+            rr += dq.x;
+            ch += dq.y;
+            if (ch >= C) {
+                ch -= C;
+                ++rr;
+            }
         }
     }
     // block statistics
@@ -377,18 +402,26 @@ __global__ void __launch_bounds__(512, 3) k_classify(const double* __restrict__ 
     block_exclusive_scan(s_scan, nrec, warp_tot);
 
     // pass 4: outputs
-    for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
-        const int2 qr = divmod_small(j, C, inv_c);
-        const int rr = qr.x, ch = qr.y;
-        const int64_t rec = (row0 + rr) * C + ch;
-        int4 info = s_info[j];
-        const int gc = s_gc[j];
-        const int rank = pp.interleave ? s_scan[j] - s_scan[0] : s_scan[ch * nrows + rr] - s_scan[ch * nrows];
-        info.w |= ((gc & 1) << kBitG) | (((gc >> 1) & 1) << kBitC) | (rank << 16);
-        // k_compact reads the placement of gridded records and of the tile's first row (whose
-        // compressed records carry a run on from the previous tile): only those are written
-        if ((gc & 1) || j < C) rinfo[rec] = info;
-        rclass[rec] = (uint8_t)gc;
+    {
+        int4* rinfo_t = rinfo + row0 * C;
+        uint8_t* rclass_t = rclass + row0 * C;
+        int rr = q0.x, ch = q0.y;
+        for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
+            int4 info = s_info[j];
+            const int gc = s_gc[j];
+            const int rank = pp.interleave ? s_scan[j] - s_scan[0] : s_scan[ch * nrows + rr] - s_scan[ch * nrows];
+            info.w |= ((gc & 1) << kBitG) | (((gc >> 1) & 1) << kBitC) | (rank << 16);
+            // k_compact reads the placement of gridded records and of the tile's first row (whose
+            // compressed records carry a run on from the previous tile): only those are written
+            if ((gc & 1) || j < C) rinfo_t[j] = info;
+            rclass_t[j] = (uint8_t)gc;
+            rr += dq.x;
+            ch += dq.y;
+            if (ch >= C) {
+                ch -= C;
+                ++rr;
+            }
+        }
     }
     for (int ch = threadIdx.x; ch < C; ch += blockDim.x)   // interleaved: one list, channel 0's
         tile_cnt[tile * C + ch] = pp.interleave ? (ch == 0 ? s_scan[nrec] - s_scan[0] : 0)
@@ -1178,7 +1211,7 @@ __global__ void __launch_bounds__(256) k_density(const double* __restrict__ uvw,
     for (int64_t rec = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; rec < n; rec += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = rec / C;
         const int ch = (int)(rec - row * C);
-        const int4 info = place(uvw, row, row_f(uvw, row), lam_inv[ch], sc[ch], lam_f[ch], sc_f[ch], flag, rec, P, pp).info;
+        const int4 info = place(uvw, row, row_f(uvw, row), lam_inv, sc, ch, lam_f[ch], sc_f[ch], flag, rec, P, pp).info;
         if (!((info.w >> kBitGd) & 1)) continue;
         const int2 xy = cell_of(info, pp.supports);
         const int gc = pp.interleave ? 0 : ch;
@@ -1241,7 +1274,7 @@ __global__ void __launch_bounds__(256) k_reweight(const double* __restrict__ uvw
     for (int64_t rec = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; rec < n; rec += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = rec / C;
         const int ch = (int)(rec - row * C);
-        const int4 info = place(uvw, row, row_f(uvw, row), lam_inv[ch], sc[ch], lam_f[ch], sc_f[ch], flag, rec, P, pp).info;
+        const int4 info = place(uvw, row, row_f(uvw, row), lam_inv, sc, ch, lam_f[ch], sc_f[ch], flag, rec, P, pp).info;
         const bool gd = (info.w >> kBitGd) & 1;
         const float* d = nullptr;
         if (gd) {
