@@ -596,6 +596,26 @@ def oracle_table_parallel(wl, planes=None, procs=None):
     return t
 
 
+# gridded entries one gridder launch may index (32-bit entry indices, with a margin)
+ENTRY_LIMIT = (1 << 31) - 1 - 1024
+
+
+def split_launches(counts, limit=ENTRY_LIMIT):
+    """Consecutive channel groups packed into gridder launches of at most `limit` gridded
+    entries each, a group's entries never split; raises ValueError if one group alone has more."""
+    launches, cur = [], 0
+    for gi, n in enumerate(counts):
+        if n > limit:
+            raise ValueError("channel group %d has %d gridded entries, more than one launch takes (%d)"
+                             % (gi, n, limit))
+        if not launches or cur + n > limit:
+            launches.append([])
+            cur = 0
+        launches[-1].append(gi)
+        cur += n
+    return launches
+
+
 def batch_grid_error(dev, plan, ot, stores=("f32",)):
     """Grid error of the batched configuration (8192^2, 64 planes, one polarisation) against the
     FP64 oracle's plain gridding on its outer-w slice: 4 channels (331-350 MHz) x 24 steps x 300
@@ -678,13 +698,7 @@ def run_batch(args, rank, world, local_rank):
         counts.append(st["gridded"])
     del wtmp, view
     torch.cuda.empty_cache()
-    launches, cur = [[]], 0
-    for gi, n in enumerate(counts):
-        if cur + n > (1 << 31) - 1 - 1024 and launches[-1]:
-            launches.append([])
-            cur = 0
-        launches[-1].append(gi)
-        cur += n
+    launches = split_launches(counts)
     wlst = wg.WorkList(wl.rows * G, G, P, max_entries=max(sum(counts[i] for i in ls) for ls in launches) + 1024)
 
     def prepare(ls, table):

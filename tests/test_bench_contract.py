@@ -38,3 +38,21 @@ def test_reference_arm_prints_one_complete_line():
 def test_fewer_than_three_warmup_steps_are_rejected():
     r = _bench("--impl", "reference", "--steps", "1", "--warmup", "2", timeout=120)
     assert r.returncode != 0 and "warmup" in r.stderr
+
+
+def test_channel_groups_are_split_over_launches_at_the_entry_limit():
+    """bench.py packs the batched workload's channel groups into gridder launches whose entries
+    fit 32-bit indices; a group is never split, and a group over the limit is an error."""
+    import pytest
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.split_launches([]) == []
+    assert bench.split_launches([3, 4, 2], limit=10) == [[0, 1, 2]]
+    assert bench.split_launches([6, 5, 4], limit=10) == [[0], [1, 2]]
+    assert bench.split_launches([10, 1, 9, 1], limit=10) == [[0], [1, 2], [3]]
+    assert bench.split_launches([0, 0], limit=0) == [[0, 1]]
+    # the batched workload's 8 groups of about 163 M entries fit one launch
+    assert bench.split_launches([163_000_000] * 8) == [list(range(8))]
+    assert bench.split_launches([700_000_000] * 4) == [[0, 1, 2], [3]]
+    with pytest.raises(ValueError, match="group 1"):
+        bench.split_launches([5, 11], limit=10)
