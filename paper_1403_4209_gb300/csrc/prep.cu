@@ -309,13 +309,12 @@ __global__ void __launch_bounds__(512, 3) k_classify(const double* __restrict__ 
     const int nrec = nrows * C;
     const int cap = rpb * C;
     int4* s_info = reinterpret_cast<int4*>(smem);
-    int* s_scan = reinterpret_cast<int*>(s_info + cap);            // [cap + 1]
-    RowF* s_row = reinterpret_cast<RowF*>(s_scan + cap + 1);       // [rpb + 1]: rows row0-1 ..
-    unsigned char* s_gc = reinterpret_cast<unsigned char*>(s_row + rpb + 1);  // [cap]
-    __shared__ int warp_tot[32];
+    int* s_cnt = reinterpret_cast<int*>(s_info + cap);             // [C]: gridded records per channel
+    RowF* s_row = reinterpret_cast<RowF*>(s_cnt + cap + 1);        // [rpb + 1]: rows row0-1 ..
     __shared__ unsigned long long s_stat[ST_N];
 
     if (threadIdx.x < ST_N) s_stat[threadIdx.x] = 0ull;
+    for (int ch = threadIdx.x; ch < C; ch += blockDim.x) s_cnt[ch] = 0;
 
     // pass 0: each row's coordinates as floats, once for all its channels
     for (int rr = threadIdx.x - 1; rr < nrows; rr += blockDim.x)
@@ -344,13 +343,17 @@ __global__ void __launch_bounds__(512, 3) k_classify(const double* __restrict__ 
     }
     __syncthreads();
 
-    // pass 2: compression indicator, g, statistics
+    // pass 2: compression indicator, g, statistics and the outputs; the gridded records of each
+    // channel (interleaved: of the tile) are counted for the tile offsets, and k_compact gives
+    // each its rank in the tile
     // per thread at most cap / blockDim records, so the counts fit 32 bits, and so do warp sums
     unsigned n_gd = 0, n_g = 0, n_c = 0, u_g = 0, u_c = 0;
     {
+        int4* rinfo_t = rinfo + row0 * C;
+        uint8_t* rclass_t = rclass + row0 * C;
         int rr = q0.x, ch = q0.y;
         for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
-            const int4 info = s_info[j];
+            int4 info = s_info[j];
             const int gd = (info.w >> kBitGd) & 1;
             int c = 0;
             // the predecessor: the previous row of the channel, or with interleaving the previous
@@ -369,8 +372,13 @@ __global__ void __launch_bounds__(512, 3) k_classify(const double* __restrict__ 
                 c = ((pinfo.w >> kBitGd) & 1) && pinfo.x == info.x && pinfo.z == info.z;
             }
             const int g = gd & (c ^ 1);
-            s_gc[j] = (unsigned char)(g | (c << 1) | (gd << 2) | (((info.w >> kBitNeg) & 1) << 3));
-            s_scan[pp.interleave ? j : ch * nrows + rr] = g;
+            const int gc = g | (c << 1) | (gd << 2) | (((info.w >> kBitNeg) & 1) << 3);
+            info.w |= (g << kBitG) | (c << kBitC);
+            // k_compact reads the placement of gridded records and of the tile's first row (whose
+            // compressed records carry a run on from the previous tile): only those are written
+            if (g || j < C) rinfo_t[j] = info;
+            rclass_t[j] = (uint8_t)gc;
+            if (g) atomicAdd(&s_cnt[pp.interleave ? 0 : ch], 1);
             if (gd) {
                 const unsigned S = (unsigned)info.y;
                 n_gd += 1;
@@ -398,34 +406,8 @@ __global__ void __launch_bounds__(512, 3) k_classify(const double* __restrict__ 
     }
     __syncthreads();
 
-    // pass 3: channel-major (interleaved: natural-order) exclusive scan of g -> rank in the tile
-    block_exclusive_scan(s_scan, nrec, warp_tot);
-
-    // pass 4: outputs
-    {
-        int4* rinfo_t = rinfo + row0 * C;
-        uint8_t* rclass_t = rclass + row0 * C;
-        int rr = q0.x, ch = q0.y;
-        for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
-            int4 info = s_info[j];
-            const int gc = s_gc[j];
-            const int rank = pp.interleave ? s_scan[j] - s_scan[0] : s_scan[ch * nrows + rr] - s_scan[ch * nrows];
-            info.w |= ((gc & 1) << kBitG) | (((gc >> 1) & 1) << kBitC) | (rank << 16);
-            // k_compact reads the placement of gridded records and of the tile's first row (whose
-            // compressed records carry a run on from the previous tile): only those are written
-            if ((gc & 1) || j < C) rinfo_t[j] = info;
-            rclass_t[j] = (uint8_t)gc;
-            rr += dq.x;
-            ch += dq.y;
-            if (ch >= C) {
-                ch -= C;
-                ++rr;
-            }
-        }
-    }
     for (int ch = threadIdx.x; ch < C; ch += blockDim.x)   // interleaved: one list, channel 0's
-        tile_cnt[tile * C + ch] = pp.interleave ? (ch == 0 ? s_scan[nrec] - s_scan[0] : 0)
-                                                : s_scan[(ch + 1) * nrows] - s_scan[ch * nrows];
+        tile_cnt[tile * C + ch] = pp.interleave ? (ch == 0 ? s_cnt[0] : 0) : s_cnt[ch];
     const int slot = (int)(tile % kNormSlots);
     if (threadIdx.x == 0) s_stat[ST_RECORDS] = (unsigned long long)nrec;
     __syncthreads();
@@ -644,13 +626,14 @@ __device__ __forceinline__ unsigned flags_of(const uint8_t* __restrict__ flag, i
     else return __ldg(flag + rec);
 }
 
-// Writes one run of a channel sequence (or of the interleaved sequence): for a head, its entry,
+// Writes one run of a channel sequence (or of the interleaved sequence): for a head of the given
+// rank among the tile's gridded records of its list, its entry,
 // gamma and run (first and last row, or record when interleaved); for the compressed records a
 // tile starts with (a carry: the end of a run begun in an earlier tile), their sum in
 // carry[tile][sequence] for k_carry.  Adds zeta(sub-kernel) x sum eps (1-f) to the normaliser.
 template <int P>
-__device__ __forceinline__ void emit_run(const int4& info, bool is_carry, int64_t tile, int C, int ch, int gch,
-                                         int64_t first, int64_t last, const float2 (&acc)[P], const float (&wsum)[P],
+__device__ __forceinline__ void emit_run(const int4& info, bool is_carry, int rank, int64_t tile, int C, int ch,
+                                         int gch, int64_t first, int64_t last, const float2 (&acc)[P], const float (&wsum)[P],
                                          const PlaceParams& pp, float* s_norm, const int* __restrict__ tile_off,
                                          const int* __restrict__ chan_base, int4* __restrict__ entries,
                                          float2* __restrict__ gamma, int2* __restrict__ runs, int64_t cap_entries,
@@ -671,7 +654,6 @@ __device__ __forceinline__ void emit_run(const int4& info, bool is_carry, int64_
         carry_last[c] = (int)last;
         return;
     }
-    const int rank = (info.w >> 16) & 0xFFFF;
     const int dst = chan_base[gch] + tile_off[tile * C + gch] + rank;
     if (dst < 0 || (int64_t)dst >= cap_entries) {   // cannot happen with a consistent scan
         atomicAdd(reinterpret_cast<unsigned long long*>(&scal[3]), 1ull);
@@ -722,7 +704,8 @@ __global__ void __launch_bounds__(kCompactThreads, 2) k_compact(const int4* __re
     float* s_norm = s_w + (size_t)cap * P;                                // [C][P]
     int* s_heads = reinterpret_cast<int*>(s_norm + (size_t)C * P);        // [cap]
     uint8_t* s_cls = reinterpret_cast<uint8_t*>(s_heads + cap);           // [cap]
-    __shared__ int n_heads;
+    int* s_first = reinterpret_cast<int*>(s_cls + ((cap + 3) & ~3));     // [C]: list position of each channel's first head
+    __shared__ int s_wtot[kCompactThreads / 32];
     __shared__ int s_abort;
     __shared__ unsigned long long s_bar;
     const int unweighted = pp.unweighted;
@@ -750,10 +733,7 @@ __global__ void __launch_bounds__(kCompactThreads, 2) k_compact(const int4* __re
             }
         }
     }
-    if (threadIdx.x == 0) {
-        n_heads = 0;
-        s_abort = 0;
-    }
+    if (threadIdx.x == 0) s_abort = 0;
     for (int i = threadIdx.x; i < C * P; i += blockDim.x) s_norm[i] = 0.f;
     __syncthreads();
     if constexpr (BULK) {
@@ -786,7 +766,6 @@ __global__ void __launch_bounds__(kCompactThreads, 2) k_compact(const int4* __re
                 const int c = cls[u];
                 s_cls[j] = (uint8_t)c;
                 if (!(c & 4)) continue;                  // not griddable
-                if (c & 1) s_heads[atomicAdd(&n_heads, 1)] = j;
                 const int64_t rec = row0 * C + j;
                 float2 v[P];
                 float w[P];
@@ -824,7 +803,6 @@ __global__ void __launch_bounds__(kCompactThreads, 2) k_compact(const int4* __re
             const int cls = rclass[rec];
             s_cls[j] = (uint8_t)cls;
             if (!(cls & 4)) continue;                       // not griddable
-            if (cls & 1) s_heads[atomicAdd(&n_heads, 1)] = j;
             const float scale = vis_scale ? vis_scale[j % C] : 1.0f;
             const bool neg = (cls >> 3) & 1;
             if (vec) {
@@ -855,12 +833,68 @@ __global__ void __launch_bounds__(kCompactThreads, 2) k_compact(const int4* __re
         return;
     }
 
+    // the tile's gridded records listed channel-major (interleaved: in natural order), which is
+    // the order of their entries: a block scan of their flags gives each one its list position,
+    // and its rank in its channel's list is that position less the channel's first one
+    int nh;
+    {
+        const int T = blockDim.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+        const int ept = (nrec + T - 1) / T;                  // list elements per thread
+        const int k0 = min(nrec, t * ept), k1 = min(nrec, k0 + ept);
+        const float inv_n = __frcp_rn((float)nrows);
+        const int2 e0 = IL ? make_int2(0, 0) : divmod_small(k0, nrows, inv_n);   // (channel, row) of element k0
+        int cnt = 0;
+        {
+            int ch = e0.x, rr = e0.y;
+            for (int k = k0; k < k1; ++k) {
+                cnt += s_cls[IL ? k : rr * C + ch] & 1;
+                if (++rr == nrows) {
+                    rr = 0;
+                    ++ch;
+                }
+            }
+        }
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (lane == 31) s_wtot[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            const int nw = T >> 5;
+            int v = lane < nw ? s_wtot[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (lane < nw) s_wtot[lane] = v;                 // inclusive over warps
+        }
+        __syncthreads();
+        int pos = inc - cnt + (wid > 0 ? s_wtot[wid - 1] : 0);
+        {
+            int ch = e0.x, rr = e0.y;
+            for (int k = k0; k < k1; ++k) {
+                const int j = IL ? k : rr * C + ch;
+                if (!IL && rr == 0) s_first[ch] = pos;
+                if (s_cls[j] & 1) s_heads[pos++] = j;
+                if (++rr == nrows) {
+                    rr = 0;
+                    ++ch;
+                }
+            }
+        }
+        nh = s_wtot[(T >> 5) - 1];
+        __syncthreads();
+    }
+
     // pass 2: work items are the tile's gridded records (runs summed inside the tile) and, per
     // sequence (channel; the one natural-order sequence when interleaved), the compressed
     // records the tile starts with, which continue a run of an earlier tile: their sum is left
     // in carry[tile][sequence] for k_carry to add to that run's entry.  A run is walked with the
     // next record's class and values loaded together (one shared-memory latency per record).
-    const int nh = n_heads;
     const int n_seq = IL ? 1 : C;
     for (int h = threadIdx.x; h < nh + n_seq; h += blockDim.x) {
         const bool is_carry = h >= nh;
@@ -901,8 +935,9 @@ __global__ void __launch_bounds__(kCompactThreads, 2) k_compact(const int4* __re
             }
         }
         const int64_t last = IL ? row0 * C + jl : row0 + jl / C;
-        emit_run<P>(info, is_carry, tile, C, ch, gch, IL ? rec : row, last, acc, wsum, pp, s_norm, tile_off, chan_base,
-                    entries, gamma, runs, cap_entries, carry_q, carry_last, scal);
+        const int rank = is_carry ? 0 : (IL ? h : h - s_first[ch]);
+        emit_run<P>(info, is_carry, rank, tile, C, ch, gch, IL ? rec : row, last, acc, wsum, pp, s_norm, tile_off,
+                    chan_base, entries, gamma, runs, cap_entries, carry_q, carry_last, scal);
     }
     __syncthreads();
     const int slot = (int)(tile % kNormSlots);
@@ -1022,7 +1057,8 @@ static size_t classify_smem(int rpb, int C)
 static size_t compact_smem(int rpb, int C, int P)
 {
     const size_t cap = (size_t)rpb * C;
-    return cap * P * (sizeof(float2) + sizeof(float)) + (size_t)C * P * sizeof(float) + cap * sizeof(int) + cap + 16;
+    return cap * P * (sizeof(float2) + sizeof(float)) + (size_t)C * P * sizeof(float) + cap * sizeof(int) +
+           ((cap + 3) & ~(size_t)3) + (size_t)C * sizeof(int) + 16;
 }
 
 static PlaceParams place_params(const Table& t, int n, double du, int C, int P, int flags)
