@@ -5,12 +5,14 @@
 //   k_classify  (PreProcessUVW, Sec. 4.3.4): FP64 placement of each record (row, chan), its
 //               griddability, the compression indicator c (eq. "ci": same footprint origin
 //               and kernel pointer as the griddable predecessor (row-1, chan)), g = gd & !c,
-//               and statistics; a block scan of g in channel-major order gives each gridded
-//               record its rank inside the tile (Index Create and Filter, Algorithm "index").
+//               and statistics; it counts each channel's gridded records in the tile (Index
+//               Create and Filter, Algorithm "index").
 //   k_scan_tiles / k_finalize: per-channel exclusive scan of the tile counts and the
 //               channel bases, so gridded records land channel-major, row-ordered.
 //   k_compact   (Compress Index Generate + Compress and Weigh Visibilities, Algorithm
-//               "compressindex", eqs. "compress1"/"conjugatetake"): each gridded record
+//               "compressindex", eqs. "compress1"/"conjugatetake"): a block scan of g in
+//               channel-major order lists the tile's gridded records and gives each its rank
+//               in its channel's part of the tile; each gridded record
 //               walks its run of compressed successors and sums eps (1-f) psi-conj(vis) (a run
 //               crossing a tile end is finished by k_carry from the next tiles' carries); the
 //               run's eps (1-f) times its sub-kernel's zeta gives the normaliser terms (eq.
